@@ -1,0 +1,355 @@
+"""ORACLE -- test infrastructure only.
+
+Plain CPU reference for the permanent of Lundow & Markstrom (arXiv:1904.06229).
+Only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline leg of `bench.py`
+may import this module.  It shares no code with the CUDA library in the
+package and never imports it.
+
+What lives here:
+  * ctypes bindings to `perm_oracle.c` (compiled on first use with gcc):
+      - Eq.(per) brute force and Eq.(ryser) plain subset sum, long double;
+      - App. A subpermanent / permanent (Gray-code walk, Neumaier-compensated
+        long double accumulation, OpenMP over parts, fixed-order sum of parts);
+      - exact 512-bit integer and multi-prime modular forms for int8 matrices.
+  * pure-Python exact arithmetic for tiny cases:
+      - Eq.(per) over all permutations with `fractions.Fraction`;
+      - one Gray-code term evaluated straight from its definition (no walk);
+      - Miller-Rabin primality and the four largest primes below 2^62;
+      - Chinese remaindering with Python integers.
+
+Sign and scaling conventions (App. A, "subpermanent" and "permanent"): the
+term of code index r is prod_i w_i(x) with x = r xor (r >> 1) and
+w_i = a_{i,n} - 1/2 sum_j a_ij + sum_{j<n, x_j=1} a_ij; the full permanent is
+2 (-1)^(n-1) sum_r (-1)^r term(r).  `glynn_partial` returns
+sum_{r in range} (-1)^r term(r) (the negative of the paper's S, whose sign t
+is flipped before each addition).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+from fractions import Fraction
+from itertools import permutations
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "perm_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_XL = 8  # 64-bit limbs of the exact integer form
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile perm_oracle.c into oracle/_build/liboracle.so (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+               "-o", tmp, _SRC]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            ld_p = ctypes.c_void_p
+            u64 = ctypes.c_uint64
+            lib.oracle_per_brute_c.argtypes = [ld_p, ctypes.c_int, ld_p]
+            lib.oracle_per_ryser_c.argtypes = [ld_p, ctypes.c_int, ld_p]
+            lib.oracle_glynn_range_c.argtypes = [ld_p, ctypes.c_int, u64, u64, ld_p, ld_p]
+            lib.oracle_glynn_part_c.argtypes = [ld_p, ctypes.c_int, u64, u64, ld_p, ld_p]
+            lib.oracle_per_glynn_c.argtypes = [ld_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ld_p, ld_p]
+            lib.oracle_glynn_exact_range_i8.argtypes = [ld_p, ctypes.c_int, u64, u64, ld_p]
+            lib.oracle_per_exact_i8.argtypes = [ld_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ld_p]
+            lib.oracle_glynn_mod_range_i8.argtypes = [ld_p, ctypes.c_int, ld_p, ctypes.c_int, u64, u64, ld_p]
+            lib.oracle_per_mod_i8.argtypes = [ld_p, ctypes.c_int, ld_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ld_p]
+            _lib = lib
+    return _lib
+
+
+def _as_c128(A) -> np.ndarray:
+    """Row-major interleaved (re, im) float64 copy of a square matrix."""
+    A = np.asarray(A)
+    if A.ndim != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("square matrix expected")
+    return np.ascontiguousarray(A.astype(np.complex128)).view(np.float64)
+
+
+def _as_i8(A) -> np.ndarray:
+    A = np.asarray(A)
+    if A.ndim != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("square matrix expected")
+    if np.any(np.abs(A.astype(np.int64)) > 127):
+        raise ValueError("entries must fit int8")
+    return np.ascontiguousarray(A.astype(np.int8))
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _ld_complex(out: np.ndarray):
+    return out[0], out[1]
+
+
+def long_double_digits() -> int:
+    return int(_load().oracle_long_double_digits())
+
+
+# ----------------------------------------------------------------- long double
+def per_brute(A):
+    """Eq.(per) summed over all permutations in long double (n <= 10).
+
+    Returns (re, im) as numpy longdouble."""
+    a = _as_c128(A)
+    out = np.zeros(2, dtype=np.longdouble)
+    if _load().oracle_per_brute_c(_ptr(a), a.shape[0], _ptr(out)) != 0:
+        raise ValueError("n out of range for brute force")
+    return _ld_complex(out)
+
+
+def per_ryser(A):
+    """Eq.(ryser): plain inclusion-exclusion over all 2^n subsets (n <= 24)."""
+    a = _as_c128(A)
+    out = np.zeros(2, dtype=np.longdouble)
+    if _load().oracle_per_ryser_c(_ptr(a), a.shape[0], _ptr(out)) != 0:
+        raise ValueError("n out of range for Ryser")
+    return _ld_complex(out)
+
+
+def per(A, parts: int = 0, threads: int = 0):
+    """App. A "permanent": Gray-code Glynn walk in `parts` parts (default: one
+    part per 2^16 codes, at least one per thread), compensated long double.
+
+    Returns (re, im, abs_sum) as numpy longdouble, abs_sum = sum over terms of
+    |2 * term| (so abs_sum / |per| is the condition number of the sum)."""
+    a = _as_c128(A)
+    n = a.shape[0]
+    total = 1 << (n - 1)
+    if parts <= 0:
+        parts = max(min(total, 64), min(total >> 16, 1 << 20))
+    out = np.zeros(2, dtype=np.longdouble)
+    asum = np.zeros(1, dtype=np.longdouble)
+    rc = _load().oracle_per_glynn_c(_ptr(a), n, int(parts), int(threads), _ptr(out), _ptr(asum))
+    if rc != 0:
+        raise ValueError(f"oracle_per_glynn_c failed ({rc})")
+    return out[0], out[1], asum[0]
+
+
+def glynn_partial(A, first: int, count: int):
+    """sum_{r=first}^{first+count-1} (-1)^r prod_i w_i(gray(r)), by the App. A
+    walk started at `first` (unrank + seed, steps 2-8) and run `count` steps.
+
+    Returns (re, im, abs_sum) as numpy longdouble."""
+    a = _as_c128(A)
+    n = a.shape[0]
+    out = np.zeros(2, dtype=np.longdouble)
+    asum = np.zeros(1, dtype=np.longdouble)
+    rc = _load().oracle_glynn_range_c(_ptr(a), n, int(first), int(count), _ptr(out), _ptr(asum))
+    if rc != 0:
+        raise ValueError("bad range")
+    # the paper's S carries t = (-1)^(r+1); negate to (-1)^r
+    return -out[0], -out[1], asum[0]
+
+
+def glynn_partial_parts(A, first: int, count: int, parts: int, threads: int = 0):
+    """Same sum as `glynn_partial`, split into `parts` sub-ranges by the paper's
+    `distribute`, evaluated in a thread pool of OpenMP-free ctypes calls and
+    added in index order with compensation (long double)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    parts = max(1, min(parts, count)) if count else 1
+    q, rem = divmod(count, parts)
+    ranges = [(first + i * q + min(i, rem), q + (1 if i < rem else 0)) for i in range(parts)]
+    workers = threads if threads > 0 else (os.cpu_count() or 1)
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        res = list(ex.map(lambda fr: glynn_partial(A, fr[0], fr[1]), ranges))
+    return _compensated([r[0] for r in res]), _compensated([r[1] for r in res]), _compensated([r[2] for r in res])
+
+
+def _compensated(xs):
+    s = np.longdouble(0)
+    c = np.longdouble(0)
+    for x in xs:
+        x = np.longdouble(x)
+        t = s + x
+        if abs(s) >= abs(x):
+            c += (s - t) + x
+        else:
+            c += (x - t) + s
+        s = t
+    return s + c
+
+
+# ------------------------------------------------------------------- integers
+def _limbs_to_int(limbs) -> int:
+    v = 0
+    for i, l in enumerate(limbs):
+        v |= int(l) << (64 * i)
+    if v >> (64 * _XL - 1):
+        v -= 1 << (64 * _XL)
+    return v
+
+
+def per_exact(A, parts: int = 0, threads: int = 0) -> int:
+    """Exact permanent of an integer (int8) matrix via the integer form of the
+    App. A walk (v = 2w), 512-bit accumulation, exact division by 2^(n-1)."""
+    a = _as_i8(A)
+    n = a.shape[0]
+    if parts <= 0:
+        parts = max(1, min(1 << (n - 1), 4096))
+    out = np.zeros(_XL, dtype=np.uint64)
+    rc = _load().oracle_per_exact_i8(_ptr(a), n, int(parts), int(threads), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle_per_exact_i8 failed ({rc})")
+    return _limbs_to_int(out)
+
+
+def glynn_exact_partial(A, first: int, count: int) -> int:
+    """Exact sum_{r in range} (-1)^r prod_i v_i(gray(r)) with v = 2w (integer A)."""
+    a = _as_i8(A)
+    out = np.zeros(_XL, dtype=np.uint64)
+    rc = _load().oracle_glynn_exact_range_i8(_ptr(a), a.shape[0], int(first), int(count), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle_glynn_exact_range_i8 failed ({rc})")
+    return -_limbs_to_int(out)
+
+
+def per_mod(A, primes, parts: int = 0, threads: int = 0):
+    """per(A) mod each prime, by the modular form of the walk (int8 A)."""
+    a = _as_i8(A)
+    n = a.shape[0]
+    pr = np.ascontiguousarray(np.asarray(primes, dtype=np.uint64))
+    if parts <= 0:
+        parts = max(1, min(1 << (n - 1), 4096))
+    out = np.zeros(len(pr), dtype=np.uint64)
+    rc = _load().oracle_per_mod_i8(_ptr(a), n, _ptr(pr), len(pr), int(parts), int(threads), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle_per_mod_i8 failed ({rc})")
+    return [int(v) for v in out]
+
+
+# ------------------------------------------------------ exact tiny references
+def _frac(x) -> Fraction:
+    return Fraction(float(x))
+
+
+def per_brute_exact(A):
+    """Eq.(per) over all n! permutations, exact rational arithmetic.
+
+    Float entries are taken at their exact binary values.  Returns a pair of
+    Fractions (re, im)."""
+    A = np.asarray(A)
+    n = A.shape[0]
+    if n > 8:
+        raise ValueError("n <= 8 for the exact brute force")
+    M = [[(_frac(np.real(A[i, j])), _frac(np.imag(A[i, j]))) for j in range(n)] for i in range(n)]
+    sr, si = Fraction(0), Fraction(0)
+    for p in permutations(range(n)):
+        pr, pi = Fraction(1), Fraction(0)
+        for i in range(n):
+            ar, ai = M[i][p[i]]
+            pr, pi = pr * ar - pi * ai, pr * ai + pi * ar
+        sr += pr
+        si += pi
+    return sr, si
+
+
+def per_brute_int(A) -> int:
+    """Eq.(per) over all n! permutations for integer A (Python integers)."""
+    A = np.asarray(A, dtype=np.int64)
+    n = A.shape[0]
+    s = 0
+    for p in permutations(range(n)):
+        t = 1
+        for i in range(n):
+            t *= int(A[i, p[i]])
+        s += t
+    return s
+
+
+def glynn_term_exact(A, r: int):
+    """One term of the halved Gray-code sum, straight from its definition:
+    (-1)^r prod_i (a_{i,n} - 1/2 sum_j a_ij + sum_{j<n: x_j=1} a_ij),
+    x = r xor (r >> 1); exact rational (re, im)."""
+    A = np.asarray(A)
+    n = A.shape[0]
+    x = r ^ (r >> 1)
+    M = [[(_frac(np.real(A[i, j])), _frac(np.imag(A[i, j]))) for j in range(n)] for i in range(n)]
+    pr, pi = Fraction(1), Fraction(0)
+    for i in range(n):
+        wr = M[i][n - 1][0] - sum(M[i][j][0] for j in range(n)) / 2
+        wi = M[i][n - 1][1] - sum(M[i][j][1] for j in range(n)) / 2
+        for j in range(n - 1):
+            if (x >> j) & 1:
+                wr += M[i][j][0]
+                wi += M[i][j][1]
+        pr, pi = pr * wr - pi * wi, pr * wi + pi * wr
+    s = -1 if r & 1 else 1
+    return s * pr, s * pi
+
+
+# ------------------------------------------------------- primes and the CRT
+def is_prime(m: int) -> bool:
+    """Deterministic Miller-Rabin for m < 3.3e24 (first twelve prime bases)."""
+    if m < 2:
+        return False
+    small = (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37)
+    for p in small:
+        if m % p == 0:
+            return m == p
+    d, s = m - 1, 0
+    while d % 2 == 0:
+        d //= 2
+        s += 1
+    for a in small:
+        y = pow(a, d, m)
+        if y in (1, m - 1):
+            continue
+        for _ in range(s - 1):
+            y = y * y % m
+            if y == m - 1:
+                break
+        else:
+            return False
+    return True
+
+
+def largest_primes_below(bound: int, k: int):
+    out = []
+    c = bound - 1
+    while len(out) < k:
+        if is_prime(c):
+            out.append(c)
+        c -= 1
+    return out
+
+
+def default_primes():
+    """The four largest primes below 2^62 (found by search, not typed in)."""
+    return largest_primes_below(1 << 62, 4)
+
+
+def crt(residues, primes) -> int:
+    """Chinese remaindering; result centred in (-P/2, P/2]."""
+    P = 1
+    for p in primes:
+        P *= p
+    x = 0
+    for r, p in zip(residues, primes):
+        Mi = P // p
+        x += int(r) * Mi * pow(Mi, -1, p)
+    x %= P
+    if x > P // 2:
+        x -= P
+    return x

@@ -1,0 +1,238 @@
+"""Pins for the CPU oracle: it is checked against what the paper and the
+mathematics fix, never against itself or the CUDA library.
+
+  * Eq.(per) brute force with exact rational arithmetic (n <= 8);
+  * worked examples under tests/golden/ (hand-derived, cited);
+  * closed forms: per(J_n) = n! (Sec. 2.B), per(I) = 1, permutation matrices,
+    per(J - I) = derangement numbers, rank one, block diagonal;
+  * invariances: row/column permutation, transpose, multilinearity;
+  * the range form against single terms computed from their definition;
+  * exact integer, modular and CRT forms against each other and brute force.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1904_06229_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "worked_examples.json")
+
+
+def _c(re, im=0):
+    return complex(float(re), float(im))
+
+
+def _ld_rel(got_re, got_im, ref_re, ref_im):
+    d = np.hypot(np.longdouble(got_re) - np.longdouble(ref_re), np.longdouble(got_im) - np.longdouble(ref_im))
+    m = np.hypot(np.longdouble(ref_re), np.longdouble(ref_im))
+    return float(d / m) if m else float(d)
+
+
+def _u_ld():
+    return 2.0 ** (1 - O.long_double_digits())
+
+
+def derangements(n):
+    d = [1, 0]
+    for k in range(2, n + 1):
+        d.append((k - 1) * (d[k - 1] + d[k - 2]))
+    return d[n]
+
+
+@pytest.mark.parametrize("n", range(1, 9))
+def test_brute_force_exact(n):
+    A = W.complex_gaussian(n, 100 + n)
+    er, ei = O.per_brute_exact(A)
+    ref = (np.longdouble(er.numerator) / np.longdouble(er.denominator),
+           np.longdouble(ei.numerator) / np.longdouble(ei.denominator))
+    tol = 64 * n * _u_ld() * 50
+    for f in (O.per_brute, O.per_ryser):
+        r = f(A) if n <= 8 else None
+        assert _ld_rel(r[0], r[1], *ref) < tol
+    g = O.per(A)
+    assert _ld_rel(g[0], g[1], *ref) < max(tol, 64 * n * _u_ld() * float(g[2] / np.hypot(*ref)))
+
+
+@pytest.mark.parametrize("case", json.load(open(GOLDEN))["cases"], ids=lambda c: c["name"])
+def test_golden_worked_examples(case):
+    A = np.array(case["matrix"], dtype=float)
+    r = O.per(A)
+    assert float(r[0]) == pytest.approx(case["per"], rel=1e-15, abs=1e-15)
+    assert abs(float(r[1])) < 1e-15
+    if np.allclose(A, np.round(A)) and np.abs(A).max() < 128:
+        assert O.per_exact(A.astype(np.int8)) == case["per"]
+        assert O.per_brute_int(A.astype(np.int64)) == case["per"]
+
+
+def test_hand_traces_small():
+    # n = 1: per = a ; n = 2: per = ad + bc (App. A traced by hand)
+    a, b, c, d = 1.25 - 0.5j, -2.0 + 0.75j, 0.5 + 3j, -1.5 - 1j
+    r = O.per(np.array([[a]]))
+    assert _c(r[0], r[1]) == a
+    r = O.per(np.array([[a, b], [c, d]]))
+    assert abs(_c(r[0], r[1]) - (a * d + b * c)) < 1e-15
+    # n = 3: sum over the six permutations written out
+    M = W.complex_gaussian(3, 7)
+    p = (M[0, 0] * M[1, 1] * M[2, 2] + M[0, 0] * M[1, 2] * M[2, 1] + M[0, 1] * M[1, 0] * M[2, 2]
+         + M[0, 1] * M[1, 2] * M[2, 0] + M[0, 2] * M[1, 0] * M[2, 1] + M[0, 2] * M[1, 1] * M[2, 0])
+    r = O.per(M)
+    assert abs(_c(r[0], r[1]) - p) < 1e-14 * abs(p)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 12, 16, 20, 24])
+def test_all_ones_factorial(n):
+    # Sec. 2.B: per(J) = n!
+    r = O.per(np.ones((n, n)))
+    assert _ld_rel(r[0], r[1], math.factorial(n), 0) < 1e-14
+    if n <= 20:
+        assert O.per_exact(np.ones((n, n), dtype=np.int8)) == math.factorial(n)
+
+
+@pytest.mark.parametrize("n", [1, 4, 9, 16])
+def test_identity_and_permutation(n):
+    r = O.per(np.eye(n))
+    assert _c(r[0], r[1]) == 1
+    P = np.eye(n)[np.random.default_rng(n).permutation(n)]
+    r = O.per(P)
+    assert abs(_c(r[0], r[1]) - 1) < 1e-15
+    assert O.per_exact(P.astype(np.int8)) == 1
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 8, 11, 14, 18])
+def test_derangements(n):
+    J = np.ones((n, n)) - np.eye(n)
+    Dn = derangements(n)
+    r = O.per(J)
+    assert _ld_rel(r[0], r[1], Dn, 0) < 1e-14
+    assert O.per_exact(J.astype(np.int8)) == Dn
+
+
+@pytest.mark.parametrize("n", [3, 6, 10, 13])
+def test_rank_one(n):
+    rng = np.random.default_rng(50 + n)
+    u = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    ref = math.factorial(n) * np.prod(u) * np.prod(v)
+    r = O.per(np.outer(u, v))
+    tol = 256 * n * _u_ld() * float(r[2]) / abs(ref) + 1e-15
+    assert abs(_c(r[0], r[1]) - ref) <= tol * abs(ref)
+
+
+def test_block_diagonal():
+    B = W.complex_gaussian(7, 1)
+    C = W.haar_submatrix(6, 36, 2)
+    M = np.zeros((13, 13), dtype=complex)
+    M[:7, :7] = B
+    M[7:, 7:] = C
+    pb, pc, pm = O.per(B), O.per(C), O.per(M)
+    ref = _c(pb[0], pb[1]) * _c(pc[0], pc[1])
+    assert abs(_c(pm[0], pm[1]) - ref) < 1e-13 * abs(ref)
+
+
+def test_invariances():
+    n = 11
+    A = W.complex_gaussian(n, 9)
+    r0 = O.per(A)
+    p0 = _c(r0[0], r0[1])
+    rng = np.random.default_rng(0)
+    for B in (A.T, A[rng.permutation(n)], A[:, rng.permutation(n)],
+              A[rng.permutation(n)][:, rng.permutation(n)]):
+        r = O.per(B)
+        assert abs(_c(r[0], r[1]) - p0) < 1e-13 * abs(p0)
+    # multilinearity in a row
+    c = 0.75 - 2.5j
+    B = A.copy()
+    B[4] *= c
+    r = O.per(B)
+    assert abs(_c(r[0], r[1]) - c * p0) < 1e-13 * abs(c * p0)
+
+
+@pytest.mark.parametrize("n", [9, 12, 14])
+def test_ryser_vs_glynn(n):
+    A = W.haar_submatrix(n, n * n, 11 + n)
+    a, b = O.per_ryser(A), O.per(A)
+    assert _ld_rel(b[0], b[1], a[0], a[1]) < 1e-13
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 6])
+def test_range_terms_from_definition(n):
+    """Every single-code range equals the term computed from its definition."""
+    A = W.complex_gaussian(n, 30 + n)
+    for r in range(1 << (n - 1)):
+        tr, ti = O.glynn_term_exact(A, r)
+        g = O.glynn_partial(A, r, 1)
+        ref = (float(tr), float(ti))
+        assert abs(_c(g[0], g[1]) - complex(*ref)) <= 1e-15 * max(1.0, abs(complex(*ref)))
+
+
+def test_range_partition_sums_to_permanent():
+    n = 13
+    A = W.complex_gaussian(n, 77)
+    N = 1 << (n - 1)
+    cuts = [0, 1, 7, 100, 1023, 1024, 3000, N - 1, N]
+    re = im = np.longdouble(0)
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        g = O.glynn_partial(A, a, b - a)
+        re += g[0]
+        im += g[1]
+    s = 2 * (-1) ** (n - 1)
+    r = O.per(A)
+    assert _ld_rel(s * re, s * im, r[0], r[1]) < 1e-14
+    g = O.glynn_partial_parts(A, 0, N, 5)
+    assert _ld_rel(s * g[0], s * g[1], r[0], r[1]) < 1e-14
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 8])
+def test_exact_integer_vs_brute(n):
+    rng = np.random.default_rng(200 + n)
+    for A in (W.zero_one(n, n), W.bernoulli_pm1(n, n), rng.integers(-127, 128, (n, n))):
+        assert O.per_exact(A) == O.per_brute_int(A)
+
+
+def test_exact_integer_partial_divisibility():
+    # the unscaled full sum is 2^(n-1) * per * (-1)^(n-1) / 2 ... checked through per_exact's own divisibility
+    n = 10
+    A = W.bernoulli_pm1(n, 3)
+    N = 1 << (n - 1)
+    tot = sum(O.glynn_exact_partial(A, a, b - a) for a, b in [(0, 5), (5, 300), (300, N)])
+    # per = 2^(1-n) (-1)^(n-1) * sum_r (-1)^r prod v_r
+    assert tot % (1 << (n - 1)) == 0
+    assert (tot >> (n - 1)) * (-1) ** (n - 1) == O.per_exact(A)
+
+
+def test_primes():
+    ps = O.default_primes()
+    assert len(ps) == 4 and len(set(ps)) == 4
+    sympy = pytest.importorskip("sympy")
+    for p in ps:
+        assert p < 2**62 and p % 2 == 1 and sympy.isprime(p)
+    # they are the four largest below 2^62
+    assert ps[0] == sympy.prevprime(2**62)
+    for a, b in zip(ps[:-1], ps[1:]):
+        assert sympy.prevprime(a) == b
+
+
+@pytest.mark.parametrize("n", [3, 9, 14])
+def test_modular_and_crt(n):
+    ps = O.default_primes()
+    for A in (W.zero_one(n, 60 + n), W.bernoulli_pm1(n, 70 + n)):
+        ex = O.per_exact(A)
+        res = O.per_mod(A, ps)
+        assert res == [ex % p for p in ps]
+        assert O.crt(res, ps) == ex
+
+
+def test_crt_signed_roundtrip():
+    ps = O.default_primes()
+    for v in (0, 1, -1, 3**100, -(7**80), (1 << 200) + 12345):
+        assert O.crt([v % p for p in ps], ps) == v
+
+
+def test_condition_number_reported():
+    A = W.complex_gaussian(12, 5)
+    r = O.per(A)
+    assert r[2] >= np.hypot(r[0], r[1])
