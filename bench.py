@@ -1,0 +1,355 @@
+"""Benchmark: Gray-code Glynn permanent throughput on the n = 40 complex128
+Haar workload (S(1600, 40): sqrt(1600) times the top-left 40 x 40 block of a
+Haar unitary of order 1600), as terms/s and as a fraction of the measured
+FP64 pipe rate; the batched random-matrix study (perms/s, batched vs one
+launch per matrix) on a sample; the CPU oracle as baseline.
+
+A step is one pass of the whole hot path (stage A, seed, Gray walk with
+product / signed accumulate / row update, double-double reduction) over one
+slice of 2^33 consecutive Gray codes of the n = 40 sum: 32 * 2^33 steps'
+worth of codes make up the whole permanent (2^39 codes), so step s covers
+slice (rank, s) of it.  Under torchrun each rank walks its own slices
+(weak scaling; the partials' exchange is a 32-byte host gather after timing).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Glynn terms/s (n=40 c128) & % FP64 peak; batched perms/s; err vs FP64 oracle"
+N_ORDER = 40
+SEED = 1040
+CODES_PER_STEP = 1 << 33
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_matrix():
+    from paper_1904_06229_gb300 import workloads as W
+
+    return W.haar_submatrix(N_ORDER, N_ORDER * N_ORDER, SEED)
+
+
+def config_dict(world):
+    return {
+        "workload": f"n={N_ORDER} complex128 Haar S({N_ORDER * N_ORDER},{N_ORDER}) seed {SEED}; "
+                    f"one step = one 2^33-code Gray slice of its permanent (2^39 codes in all)",
+        "n": N_ORDER,
+        "codes_per_step": CODES_PER_STEP,
+        "matrix_bytes": 16 * N_ORDER * N_ORDER,
+        "l2": "flushed between steps (256 MiB write); the 25.6 KB input is staged to shared memory once per block",
+        "parallelism": f"gray-range shards x{world}",
+    }
+
+
+# ------------------------------------------------------------------ helpers
+class Clocks:
+    """Samples nvidia-smi during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(A, target_s: float = 12.0):
+    """Time the oracle (as it stands) on a slice of the same sum, on all host cores."""
+    from oracle import oracle as O
+
+    cores = os.cpu_count() or 1
+    n = A.shape[0]
+    first = 1 << 30
+    count = 1 << 14
+    t0 = time.perf_counter()
+    O.glynn_partial_parts(A, first, count, parts=cores, threads=cores)
+    dt = time.perf_counter() - t0
+    # grow the sample to about target_s seconds of CPU work
+    count = int(min(1 << 26, max(count, count * target_s / max(dt, 1e-3))))
+    count = max(cores, count - count % cores)
+    t0 = time.perf_counter()
+    g = O.glynn_partial_parts(A, first, count, parts=cores, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": count / dt, "unit": "terms/s", "cores": cores, "kind": "oracle",
+            "sample": f"codes [2^30, 2^30+{count}) of the n={n} sum, long double ({O.long_double_digits()}-bit "
+                      f"significand) Neumaier-compensated App. A walk, {cores} threads",
+            "seconds": dt}, (first, count, g)
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+
+    A = workload_matrix()
+    cores = os.cpu_count() or 1
+    # each step: a bounded slice of the same workload, sized so the whole run
+    # stays within a few minutes
+    probe = 1 << 12
+    t0 = time.perf_counter()
+    O.glynn_partial_parts(A, 0, probe, parts=cores, threads=cores)
+    rate = probe / max(time.perf_counter() - t0, 1e-4)
+    per_step = int(max(cores, min(1 << 26, rate * 120.0 / max(1, args.steps + args.warmup))))
+    for w in range(args.warmup):
+        O.glynn_partial_parts(A, w * per_step, per_step, parts=cores, threads=cores)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        O.glynn_partial_parts(A, (args.warmup + s) * per_step, per_step, parts=cores, threads=cores)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    line = {"metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "long double", "data": "synthetic",
+            "impl": "reference", "config": config_dict(1),
+            "cpu_baseline": {"value": value, "unit": "terms/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} consecutive codes per step of the n={N_ORDER} sum"},
+            "e2e": {"value": value, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1904_06229_gb300 import perm as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group(backend="nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    P.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    A = workload_matrix()
+    dA = torch.from_numpy(A.astype(np.complex128)).to(dev)
+    out = torch.empty(4, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    total_codes = 1 << (N_ORDER - 1)
+    nslices = total_codes // CODES_PER_STEP
+
+    def slice_first(step):
+        return ((rank + world * step) % nslices) * CODES_PER_STEP
+
+    peak_gops = P.perm_fp64_peak()
+
+    # warm-up
+    for w in range(args.warmup):
+        P.perm_c128_range(dA, slice_first(w), CODES_PER_STEP, out=out)
+        flush.fill_(float(w))
+    torch.cuda.synchronize()
+    assert P.perm_last_status() == 0
+
+    # timed region: K steps, barrier + synchronize on both sides
+    clocks = Clocks(local)
+    partials = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        ev[s][0].record(stream)
+        P.perm_c128_range(dA, slice_first(args.warmup + s), CODES_PER_STEP, out=out)
+        ev[s][1].record(stream)
+        partials.append(out.clone())
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    launch_s = [a.elapsed_time(b) / 1e3 for a, b in ev]
+    if world > 1:
+        tt = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    terms = CODES_PER_STEP * args.steps * world
+    value = terms / elapsed
+
+    # end to end through the C ABI with host buffers (pinned): the library
+    # copies A in and the partial out inside the timed region
+    hA = torch.from_numpy(A.astype(np.complex128)).pin_memory()
+    hout = torch.empty(4, dtype=torch.float64).pin_memory()
+    for w in range(min(args.warmup, 1)):
+        P.perm_c128_range(hA, slice_first(w), CODES_PER_STEP, out=hout, stream=stream)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    h0 = time.perf_counter()
+    for s in range(e2e_steps):
+        P.perm_c128_range(hA, slice_first(args.warmup + s), CODES_PER_STEP, out=hout, stream=stream)
+        stream.synchronize()
+        _ = float(hout[0])
+    e2e_el = time.perf_counter() - h0
+    if world > 1:
+        tt = torch.tensor([e2e_el], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_el = float(tt.item())
+    e2e_value = CODES_PER_STEP * e2e_steps * world / e2e_el
+
+    # fixed-order host gather of the partials (the exchange step of a split sum)
+    if world > 1:
+        gathered = [None] * world
+        dist.all_gather_object(gathered, [p.cpu().tolist() for p in partials])
+
+    n = N_ORDER
+    ops_per_term = 6 * n - 4     # FP64 pipe ops: 4(n-1) product + 2n row update
+    flops_per_term = 8 * n - 6   # complex multiply = 6 flops, complex add = 2
+    avg_launch = sum(launch_s) / len(launch_s)
+    achieved = CODES_PER_STEP * ops_per_term / avg_launch / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
+                "frac": achieved / peak_gops, "traffic": None,
+                "kernel": f"perm::k_walk<{n}, complex, FP64 product>",
+                "ops_per_term": ops_per_term,
+                "flop_frac": CODES_PER_STEP * flops_per_term / avg_launch / (2e9 * peak_gops),
+                "peak_source": "measured this run: perm_fp64_peak() DFMA probe (MEASURED_PEAKS.json has no FP64 "
+                               "figure)"}
+    line = {"metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(world), "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": "terms/s", "h2d_bytes_per_step": 16 * n * n,
+                    "d2h_bytes_per_step": 32, "steps": e2e_steps},
+            "gpu_launches": 2 * args.steps, "clocks": clk, "fp64_peak_gops": peak_gops}
+
+    if rank == 0 and args.batch_sample > 0:
+        line["batch"] = batch_measure(P, torch, dev, args.batch_sample)
+    if rank == 0 and not args.no_cpu_baseline:
+        cb, (first, count, g) = cpu_oracle_sample(A)
+        line["cpu_baseline"] = cb
+        # error of the GPU on the very slice the oracle walked
+        o = P.perm_c128_range(dA, first, count).cpu().numpy()
+        got = complex(o[0] + o[1], o[2] + o[3])
+        ref = complex(float(g[0]), float(g[1]))
+        line["err_vs_oracle"] = {"slice": [first, count], "rel": abs(got - ref) / abs(ref),
+                                 "kappa_slice": float(g[2]) / abs(ref)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def batch_measure(P, torch, dev, sample):
+    """The batch study's distribution (n ~ U{12..28}, half Gaussian half Haar,
+    shuffled; seed 3) on `sample` matrices: one persistent graph launch vs one
+    perm_c128 launch per matrix."""
+    from paper_1904_06229_gb300 import workloads as W
+
+    ns, mats = W.batch_study(sample, seed=3)
+    dm = [torch.from_numpy(m.astype(np.complex128)).to(dev) for m in mats]
+    ptrs = torch.tensor([m.data_ptr() for m in dm], dtype=torch.int64, device=dev)
+    out = torch.empty((sample, 2), dtype=torch.float64, device=dev)
+    P.perm_batch(dm, out=out, ptrs=ptrs)  # tunes unseen orders, captures the graph
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    P.perm_batch(dm, out=out, ptrs=ptrs)
+    e1.record()
+    torch.cuda.synchronize()
+    tb = e0.elapsed_time(e1) / 1e3
+    single = torch.empty((sample, 2), dtype=torch.float64, device=dev)
+    for k in range(min(sample, 50)):
+        P.perm_c128(dm[k], out=single[k])
+    torch.cuda.synchronize()
+    e0.record()
+    for k in range(sample):
+        P.perm_c128(dm[k], out=single[k])
+    e1.record()
+    torch.cuda.synchronize()
+    ts = e0.elapsed_time(e1) / 1e3
+    d = (out - single).abs().max().item()
+    scale = single.abs().max().item()
+    terms = int(sum(1 << (int(n) - 1) for n in ns))
+    return {"sample": sample, "orders": "12..28", "terms": terms, "batched_perms_per_s": sample / tb,
+            "per_launch_perms_per_s": sample / ts, "speedup": ts / tb, "batched_terms_per_s": terms / tb,
+            "max_abs_diff_vs_per_launch": d, "max_abs_value": scale, "gpu_launches_batched": 2}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--batch-sample", type=int, default=2000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,162 @@
+/*
+ * perm.h -- C ABI of the GB300 (sm_103a) permanent library `libperm.so`.
+ *
+ * The library computes matrix permanents (Eq. per of Lundow & Markstrom,
+ * arXiv:1904.06229, Sec. 1) by the Gray-code ordered, halved inclusion-
+ * exclusion sum of Sec. 2.A and Appendix A (Nijenhuis-Wilf / Glynn form of
+ * Ryser's Eq. ryser):
+ *
+ *   per(A) = 2 (-1)^(n-1) sum_{r=0}^{2^(n-1)-1} (-1)^r prod_{i=1}^{n} w_i(x(r)),
+ *   x(r)   = r xor (r >> 1)                   (Gray code of r, bit x_1 = LSB),
+ *   w_i(x) = a_{i,n} - 1/2 sum_{j=1}^{n} a_{i,j} + sum_{j<n, x_j=1} a_{i,j}.
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are n x n, row-major, densely packed.  Complex matrices are
+ *     interleaved (re, im) doubles: 2*n*n doubles.
+ *   - Unless stated otherwise a pointer may be device memory or host memory
+ *     (pinned or pageable); host inputs are copied in and host outputs copied
+ *     out on `stream`.  A host output is valid once `stream` has been
+ *     synchronised.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Every compute call is asynchronous on `stream` and returns a
+ *     perm_status at once: argument errors are reported before anything is
+ *     launched; errors found on the device (non-finite input) are reported by
+ *     perm_last_status().
+ *   - The caller owns every buffer it passes.  The library allocates only
+ *     per-call scratch (stream-ordered, released on `stream`) and one status
+ *     word per device, released by perm_shutdown().
+ *   - Results are deterministic for a given GPU model: partial sums are
+ *     combined in a fixed order, never with floating-point atomics.
+ *   - The library never falls back to the CPU.  Without a CUDA device every
+ *     compute call returns PERM_ECUDA.
+ */
+#ifndef PERM_H_
+#define PERM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Largest supported order: the Gray index 0 <= r < 2^(n-1) is a uint64. */
+#define PERM_NMAX 64
+
+typedef enum {
+  PERM_OK = 0,
+  PERM_EINVAL = -1,     /* n < 1, n > PERM_NMAX, count < 0, range outside [0, 2^(n-1)) */
+  PERM_ENULL = -2,      /* a required pointer is NULL */
+  PERM_ECUDA = -3,      /* a CUDA runtime call failed (no device, launch failure, ...) */
+  PERM_ENONFINITE = -4, /* an input entry was NaN or Inf (reported by perm_last_status) */
+  PERM_ETIMEOUT = -5,   /* perm_last_status gave up waiting for the stream */
+  PERM_ENOMEM = -6,     /* scratch allocation failed */
+  PERM_EPRIME = -7      /* a modulus is even, < 3, >= 2^62, or repeated */
+} perm_status;
+
+/* ---- FP64 permanents (Sec. 2.A, App. A; precision scheme of Sec. 2.B) ----
+ * Row sums w_i and products in FP64, one fused multiply-add per row-sum update;
+ * each thread's terms are summed in FP64 over runs of at most 4096 codes and
+ * folded into a double-double accumulator; runs restart w from its
+ * definition (bounding incremental drift); the per-thread accumulators are
+ * combined with warp shuffles and a fixed-order tree in double-double.
+ * out: the permanent, double-double rounded to double(s). */
+
+/* Complex permanent. A: 2*n*n doubles (interleaved). out: 2 doubles (re, im). */
+int perm_c128(const double* A, int n, double* out, void* stream);
+
+/* Real permanent. A: n*n doubles. out: 1 double. */
+int perm_f64(const double* A, int n, double* out, void* stream);
+
+/* Partial Gray-code sum over the code range [first, first + count) of App. A
+ * (the sum "subpermanent" computes for one part), without the final
+ * 2 (-1)^(n-1) factor:
+ *   partial = sum_{r=first}^{first+count-1} (-1)^r prod_i w_i(x(r)).
+ * Requires first + count <= 2^(n-1).  count = 0 gives a zero partial.
+ * partial_dd (complex): 4 doubles {re_hi, re_lo, im_hi, im_lo};
+ * partial_dd (real):    2 doubles {hi, lo}.
+ * Summing the partials of disjoint ranges that cover [0, 2^(n-1)) and
+ * multiplying by 2 (-1)^(n-1) gives the permanent; this is how a long
+ * computation is split across launches, streams, processes or GPUs, and how
+ * it is checkpointed (state = next code index + partial). */
+int perm_c128_range(const double* A, int n, uint64_t first, uint64_t count, double* partial_dd, void* stream);
+int perm_f64_range(const double* A, int n, uint64_t first, uint64_t count, double* partial_dd, void* stream);
+
+/* ---- FP32-product variant (precision schemes of Sec. 2.B: product precision
+ * chosen apart from sum precision) ----
+ * Row sums and the accumulation as in perm_c128 / perm_f64 (FP64, double-
+ * double); each factor w_i is split into an integer power of two and an FP32
+ * significand in [1, 2) (per term, by bit operations), the product of the n
+ * significands is formed in FP32 and the exponents are added in integers; the
+ * term is rebuilt as a double.  Relative error per term about n * 2^-24; the
+ * result's error is reported against the FP64 oracle by the tests. */
+int perm_c128_f32p(const double* A, int n, double* out, void* stream);
+int perm_f64_f32p(const double* A, int n, double* out, void* stream);
+
+/* ---- Batch of independent complex permanents (the random-matrix studies of
+ * Secs. 3-6 need 10^5..10^7 permanents of orders up to ~35) ----
+ * ptrs: DEVICE array of `count` DEVICE pointers, each to a 2*n_k*n_k complex
+ *       matrix; ns: HOST array of the `count` orders (1 <= n_k <= 40);
+ * out:  DEVICE array of 2*count doubles (re, im per matrix).
+ * All permanents run in one persistent kernel that takes (matrix, chunk) work
+ * items, largest order first, from an atomic ticket; per-matrix partials are
+ * combined in a fixed order by a second kernel.  The launch pair is captured
+ * in a CUDA graph keyed by (ns, count) and replayed on later calls with the
+ * same sizes.  Chunk lengths come from a per-(GPU, n) tuning table that the
+ * library fills by timing candidates the first time an order is seen (see
+ * perm_batch_autotune).  Results equal perm_c128 on the same matrix to within
+ * rounding of the summation order. */
+int perm_batch(const double* const* ptrs, const int* ns, int count, double* out, void* stream);
+
+/* Fill the batch tuning table for orders n_lo..n_hi on the current device by
+ * timing candidate chunk lengths on synthetic input (blocking).  Optional:
+ * perm_batch tunes lazily.  Returns PERM_OK or an error. */
+int perm_batch_autotune(int n_lo, int n_hi);
+
+/* ---- Exact permanents of small-integer matrices ----
+ * Glynn's form (the App. A sum with v = 2w, an integer for integer A):
+ *   2^(n-1) per(A) = (-1)^(n-1) sum_r (-1)^r prod_i v_i(x(r)),
+ *   v_i(x) = 2 a_{i,n} - sum_j a_{i,j} + 2 sum_{j<n, x_j=1} a_{i,j},
+ * evaluated modulo each of four odd primes below 2^62 (64-bit Montgomery
+ * arithmetic), then multiplied by (-1)^(n-1) / 2^(n-1) mod p.
+ * A: n*n int8 entries (any value, |a| <= 127).  primes: HOST array of 4
+ * distinct odd moduli in [3, 2^62) (primality is the caller's promise; see
+ * perm_default_primes).  residues: 4 uint64, per(A) mod primes[q] in [0, p).
+ * Exact when |per(A)| < P/2, P = product of the moduli (about 2^247); the
+ * sizes of 0-1 and +-1 matrices up to n = 64 satisfy this. */
+int perm_mod01(const int8_t* A, int n, const uint64_t* primes, uint64_t* residues, void* stream);
+
+/* Chinese remaindering on the host (no GPU): residues (k values, HOST) modulo
+ * primes (k HOST values, pairwise coprime, product < 2^256) -> the unique x
+ * with |x| <= P/2 congruent to them, as a 256-bit two's-complement integer in
+ * out_limbs[4] (little-endian 64-bit limbs).  k in 1..4. */
+int perm_crt(const uint64_t* residues, const uint64_t* primes, int k, uint64_t* out_limbs);
+
+/* The four largest primes below 2^62 (deterministic Miller-Rabin search on
+ * the host), in decreasing order. */
+int perm_default_primes(uint64_t* out4);
+
+/* ---- Status, measurement and teardown ---- */
+
+/* Wait for `stream` (at most PERM_TIMEOUT_S seconds from the environment,
+ * default 86400; PERM_ETIMEOUT if exceeded), then return and clear the first
+ * error the device recorded since the last call (PERM_ENONFINITE), or
+ * PERM_OK; PERM_ECUDA if the stream itself failed. */
+int perm_last_status(void* stream);
+
+/* Human-readable name of a perm_status value (static string). */
+const char* perm_status_string(int status);
+
+/* FP64 fused-multiply-add throughput of the current device, measured with
+ * independent DFMA chains on every SM (blocking, about 0.1 s).  gops: lane
+ * DFMA operations per second / 1e9 (one DFMA = 2 flops). */
+int perm_fp64_peak(double* gops);
+
+/* Free the library's per-device status words, cached graphs and the stream-
+ * ordered memory pool's unused reserve.  Safe to call more than once. */
+void perm_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PERM_H_ */

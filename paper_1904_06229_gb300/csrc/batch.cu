@@ -1,0 +1,449 @@
+// Batched permanents: many independent complex matrices of uneven order in
+// one persistent launch (the random-matrix studies of Secs. 3-6 compute
+// 10^5..10^7 permanents of orders up to ~35 each).
+//
+// Work is cut into (matrix, code range) items of 32 lanes x L codes, L tuned
+// per order; the host sorts items by decreasing order (largest work first)
+// and each warp of the persistent grid pulls the next item from an atomic
+// ticket, stages that matrix into its own shared-memory slot, walks its range
+// with the same per-thread Gray walk as the single-matrix kernel, and writes
+// a double-double partial per item.  A second kernel adds each matrix's item
+// partials in item order (deterministic) and applies 2 (-1)^(n-1).  The pair
+// of launches (plus the ticket reset) is captured once per (device, stream,
+// pointers, orders) into a CUDA graph and replayed.
+//
+// Tuning: for each order n the codes-per-lane L is chosen by timing the
+// candidates on a synthetic batch the first time n is seen (or by
+// perm_batch_autotune); PERM_BATCH_TUNE=0 keeps the built-in default.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <list>
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "glynn_walk.cuh"
+#include "perm.h"
+#include "perm_internal.h"
+
+namespace perm {
+
+constexpr int kBatchNMax = 32;
+constexpr int kBatchThreads = 128;
+constexpr int kBatchWarps = kBatchThreads / 32;
+constexpr size_t kBatchSlot = (size_t)kBatchNMax * kBatchNMax + kBatchNMax;  // double2 per warp slot
+constexpr size_t kBatchSmem = kBatchSlot * kBatchWarps * sizeof(double2);
+
+template <int K>
+__device__ __forceinline__ void batch_walk_case(int n, const double2* sA, const double2* sW0, uint64_t r, uint64_t end,
+                                                dd& accr, dd& acci) {
+  if constexpr (K <= kBatchNMax) {
+    if (n == K) {
+      thread_walk_c128<K, kProdF64>(sA, sW0, r, end, accr, acci);
+      return;
+    }
+    batch_walk_case<K + 1>(n, sA, sW0, r, end, accr, acci);
+  }
+}
+
+__global__ void __launch_bounds__(kBatchThreads) k_batch(const double* const* __restrict__ ptrs,
+                                                         const BatchItem* __restrict__ items, int nitems,
+                                                         double* __restrict__ item_partials,
+                                                         unsigned int* __restrict__ ticket, int* __restrict__ status) {
+  extern __shared__ __align__(16) double2 bsm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double2* sA = bsm + (size_t)warp * kBatchSlot;
+  for (;;) {
+    unsigned int it = 0;
+    if (lane == 0) it = atomicAdd(ticket, 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= (unsigned int)nitems) break;
+    const BatchItem item = items[it];
+    const int n = (int)item.n;
+    const double2* __restrict__ A = reinterpret_cast<const double2*>(ptrs[item.matrix]);
+    double2* sW0 = sA + n * n;
+    // stage column-major (the single-matrix kernel's layout)
+    int bad = 0;
+    for (int idx = lane; idx < n * n; idx += 32) {
+      const int i = idx / n, j = idx - i * n;
+      const double2 v = A[idx];
+      bad |= (not_finite(v.x) || not_finite(v.y)) ? 1 : 0;
+      sA[j * n + i] = v;
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, (int)kStatusNonFinite);
+    __syncwarp();
+    if (lane < n) {
+      double sr = 0.0, si = 0.0;
+      for (int j = 0; j < n; ++j) {
+        sr += sA[j * n + lane].x;
+        si += sA[j * n + lane].y;
+      }
+      const double2 last = sA[(n - 1) * n + lane];
+      sW0[lane] = make_double2(fma(-0.5, sr, last.x), fma(-0.5, si, last.y));
+    }
+    __syncwarp();
+    // this lane's share of the item ("distribute" over 32 lanes)
+    const uint64_t q = item.count / 32, rem = item.count % 32;
+    const uint64_t r = item.first + lane * q + ((uint64_t)lane < rem ? lane : rem);
+    const uint64_t end = r + q + ((uint64_t)lane < rem ? 1 : 0);
+    dd accr{0.0, 0.0}, acci{0.0, 0.0};
+    batch_walk_case<1>(n, sA, sW0, r, end, accr, acci);
+    accr = dd_warp_sum(accr);
+    acci = dd_warp_sum(acci);
+    if (lane == 0) {
+      double* o = item_partials + (size_t)it * 4;
+      o[0] = accr.hi;
+      o[1] = accr.lo;
+      o[2] = acci.hi;
+      o[3] = acci.lo;
+    }
+    __syncwarp();
+  }
+}
+
+// out[2k..2k+1] = 2 (-1)^(n_k - 1) * sum of matrix k's item partials, in item order.
+__global__ void k_batch_finalize(const double* __restrict__ item_partials, const int* __restrict__ mat_first,
+                                 const int* __restrict__ mat_items, const int* __restrict__ mat_n, int count,
+                                 double* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  dd ar{0.0, 0.0}, ai{0.0, 0.0};
+  const int f = mat_first[k], c = mat_items[k];
+  for (int t = 0; t < c; ++t) {
+    const double* p = item_partials + (size_t)(f + t) * 4;
+    ar = dd_add(ar, dd{p[0], p[1]});
+    ai = dd_add(ai, dd{p[2], p[3]});
+  }
+  const double s = ((mat_n[k] - 1) & 1) ? -2.0 : 2.0;
+  out[2 * k] = s * __dadd_rn(ar.hi, ar.lo);
+  out[2 * k + 1] = s * __dadd_rn(ai.hi, ai.lo);
+}
+
+int batch_resident_blocks() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (cached[dev]) return cached[dev];
+  if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) != cudaSuccess)
+    return 0;
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBatchThreads, kBatchSmem) != cudaSuccess)
+    return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  cached[dev] = (per_sm < 1 ? 1 : per_sm) * sms;
+  return cached[dev];
+}
+
+}  // namespace perm
+
+using namespace perm;
+
+namespace {
+
+std::mutex g_batch_mu;
+
+// ---- tuning table: codes per lane L for each (device, order) ----
+struct Tune {
+  int L[kBatchNMax + 1] = {0};
+};
+Tune g_tune[64];
+
+int default_L(int n) {
+  // about 16 n codes per lane keeps the O(n^2) seed near 2% of the walk
+  int L = 64;
+  while (L < 16 * n && L < 4096) L <<= 1;
+  return L;
+}
+
+bool tuning_enabled() {
+  const char* e = std::getenv("PERM_BATCH_TUNE");
+  return !(e && e[0] == '0');
+}
+
+int status_of_b(cudaError_t e) {
+  if (e == cudaSuccess) return PERM_OK;
+  if (e == cudaErrorMemoryAllocation) return PERM_ENOMEM;
+  return PERM_ECUDA;
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
+int* batch_status_word(int dev) {
+  int* w = nullptr;
+  return device_status_word(dev, &w) == 0 ? w : nullptr;
+}
+
+// Build the item list for `ns` with the given per-order L; matrices sorted
+// by decreasing order, each matrix's items contiguous.
+void build_items(const int* ns, int count, const int* Ltab, std::vector<BatchItem>& items, std::vector<int>& mfirst,
+                 std::vector<int>& mcount) {
+  std::vector<int> order(count);
+  for (int k = 0; k < count; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ns[a] > ns[b]; });
+  items.clear();
+  mfirst.assign(count, 0);
+  mcount.assign(count, 0);
+  for (int k : order) {
+    const int n = ns[k];
+    const uint64_t total = 1ull << (n - 1);
+    const uint64_t per_item = 32ull * (uint64_t)Ltab[n];
+    mfirst[k] = (int)items.size();
+    for (uint64_t f = 0; f < total; f += per_item) {
+      BatchItem it;
+      it.matrix = (uint32_t)k;
+      it.n = (uint32_t)n;
+      it.first = f;
+      it.count = std::min(per_item, total - f);
+      items.push_back(it);
+    }
+    mcount[k] = (int)items.size() - mfirst[k];
+  }
+}
+
+struct Plan {
+  int dev = -1;
+  cudaStream_t stream = nullptr;
+  const void* ptrs = nullptr;
+  void* out = nullptr;
+  std::vector<int> ns;
+  std::vector<int> Ls;
+  DevBuf items, partials, mfirst, mcount, mn, ticket;
+  int nitems = 0;
+  cudaGraphExec_t exec = nullptr;
+  ~Plan() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+std::list<std::unique_ptr<Plan>> g_plans;  // most recent first
+constexpr size_t kMaxPlans = 8;
+
+int enqueue_batch(const double* const* ptrs, const BatchItem* d_items, int nitems, double* d_partials,
+                  const int* d_mfirst, const int* d_mcount, const int* d_mn, int count, unsigned int* d_ticket,
+                  double* out, int* status, cudaStream_t s) {
+  const int grid = batch_resident_blocks();
+  if (grid < 1) return PERM_ECUDA;
+  cudaError_t e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return status_of_b(e);
+  k_batch<<<grid, kBatchThreads, kBatchSmem, s>>>(ptrs, d_items, nitems, d_partials, d_ticket, status);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return status_of_b(e);
+  if (out) {
+    k_batch_finalize<<<(count + 127) / 128, 128, 0, s>>>(d_partials, d_mfirst, d_mcount, d_mn, count, out);
+    e = cudaGetLastError();
+  }
+  return status_of_b(e);
+}
+
+// Time one candidate L for order n on a synthetic batch (blocking).
+int time_candidate(int n, int L, const double* const* d_ptrs, int m, double* ms_out) {
+  std::vector<int> ns(m, n);
+  int Ltab[kBatchNMax + 1];
+  for (int k = 0; k <= kBatchNMax; ++k) Ltab[k] = L;
+  std::vector<BatchItem> items;
+  std::vector<int> mf, mc;
+  build_items(ns.data(), m, Ltab, items, mf, mc);
+  DevBuf di, dp, dt;
+  if (cudaMalloc(&di.p, items.size() * sizeof(BatchItem)) != cudaSuccess) return PERM_ENOMEM;
+  if (cudaMalloc(&dp.p, items.size() * 4 * sizeof(double)) != cudaSuccess) return PERM_ENOMEM;
+  if (cudaMalloc(&dt.p, sizeof(unsigned int)) != cudaSuccess) return PERM_ENOMEM;
+  cudaMemcpy(di.p, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int* status = batch_status_word(dev);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int rc = PERM_OK;
+  for (int rep = 0; rep < 3 && rc == PERM_OK; ++rep) {
+    cudaEventRecord(e0, nullptr);
+    rc = enqueue_batch(d_ptrs, (BatchItem*)di.p, (int)items.size(), (double*)dp.p, nullptr, nullptr, nullptr, 0,
+                       (unsigned int*)dt.p, nullptr, status, nullptr);
+    cudaEventRecord(e1, nullptr);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = PERM_ECUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = best;
+  return rc;
+}
+
+int autotune_order(int dev, int n) {
+  if (g_tune[dev].L[n]) return PERM_OK;
+  if (!tuning_enabled() || n < 4) {
+    g_tune[dev].L[n] = default_L(n);
+    return PERM_OK;
+  }
+  // synthetic matrix (fixed linear congruential values in [-1, 1)), replicated
+  // so the batch carries at least 2^24 codes
+  std::vector<double> h(2 * n * n);
+  uint64_t st = 0x9E3779B97F4A7C15ull ^ (uint64_t)n;
+  for (auto& v : h) {
+    st = st * 6364136223846793005ull + 1442695040888963407ull;
+    v = (double)(int64_t)(st >> 11) / (double)(1ull << 52) - 1.0;
+  }
+  const uint64_t per = 1ull << (n - 1);
+  int m = (int)std::max<uint64_t>(1, (1ull << 24) / per);
+  DevBuf dA, dptrs;
+  if (cudaMalloc(&dA.p, h.size() * sizeof(double)) != cudaSuccess) return PERM_ENOMEM;
+  if (cudaMalloc(&dptrs.p, (size_t)m * sizeof(double*)) != cudaSuccess) return PERM_ENOMEM;
+  cudaMemcpy(dA.p, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
+  std::vector<const double*> hp(m, (const double*)dA.p);
+  cudaMemcpy(dptrs.p, hp.data(), (size_t)m * sizeof(double*), cudaMemcpyHostToDevice);
+  double best_rate = 0.0;
+  int bestL = default_L(n);
+  for (int L = 16; L <= 8192; L <<= 1) {
+    if (32ull * L > per * 4 && L > 16) break;  // items much larger than a matrix: no new candidates
+    double ms = 0;
+    int rc = time_candidate(n, L, (const double* const*)dptrs.p, m, &ms);
+    if (rc) return rc;
+    const double rate = (double)per * m / ms;
+    if (rate > best_rate * 1.01) best_rate = rate, bestL = L;
+  }
+  g_tune[dev].L[n] = bestL;
+  return PERM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int perm_batch_autotune(int n_lo, int n_hi) {
+  if (n_lo < 1 || n_hi > kBatchNMax || n_lo > n_hi) return PERM_EINVAL;
+  int count = 0, dev = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count < 1) {
+    cudaGetLastError();
+    return PERM_ECUDA;
+  }
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return PERM_ECUDA;
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (int n = n_lo; n <= n_hi; ++n) {
+    g_tune[dev].L[n] = 0;
+    int rc = autotune_order(dev, n);
+    if (rc) return rc;
+  }
+  return PERM_OK;
+}
+
+int perm_batch(const double* const* ptrs, const int* ns, int count, double* out, void* stream) {
+  if (!ptrs || !ns || !out) return PERM_ENULL;
+  if (count < 1) return PERM_EINVAL;
+  for (int k = 0; k < count; ++k)
+    if (ns[k] < 1 || ns[k] > kBatchNMax) return PERM_EINVAL;
+  int ndev = 0, dev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return PERM_ECUDA;
+  }
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return PERM_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  int* status = batch_status_word(dev);
+  if (!status) return PERM_ENOMEM;
+  if (batch_resident_blocks() < 1) return PERM_ECUDA;
+
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  bool seen[kBatchNMax + 1] = {false};
+  for (int k = 0; k < count; ++k) seen[ns[k]] = true;
+  for (int n = 1; n <= kBatchNMax; ++n) {
+    if (!seen[n] || g_tune[dev].L[n]) continue;
+    if (cap != cudaStreamCaptureStatusNone) {
+      g_tune[dev].L[n] = default_L(n);  // no timing while the caller captures
+    } else {
+      int rc = autotune_order(dev, n);
+      if (rc) return rc;
+    }
+  }
+
+  // plan lookup
+  Plan* plan = nullptr;
+  for (auto it = g_plans.begin(); it != g_plans.end(); ++it) {
+    Plan* p = it->get();
+    if (p->dev == dev && p->stream == s && p->ptrs == (const void*)ptrs && p->out == (void*)out &&
+        (int)p->ns.size() == count && std::memcmp(p->ns.data(), ns, count * sizeof(int)) == 0) {
+      bool sameL = true;
+      for (int n = 1; n <= kBatchNMax; ++n)
+        if (seen[n] && p->Ls[n] != g_tune[dev].L[n]) sameL = false;
+      if (!sameL) break;
+      g_plans.splice(g_plans.begin(), g_plans, it);
+      plan = p;
+      break;
+    }
+  }
+  if (!plan) {
+    auto np = std::make_unique<Plan>();
+    np->dev = dev;
+    np->stream = s;
+    np->ptrs = ptrs;
+    np->out = out;
+    np->ns.assign(ns, ns + count);
+    np->Ls.assign(g_tune[dev].L, g_tune[dev].L + kBatchNMax + 1);
+    std::vector<BatchItem> items;
+    std::vector<int> mf, mc;
+    build_items(ns, count, g_tune[dev].L, items, mf, mc);
+    np->nitems = (int)items.size();
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&np->items.p, items.size() * sizeof(BatchItem));
+    if (e == cudaSuccess) e = cudaMalloc(&np->partials.p, items.size() * 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&np->mfirst.p, count * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&np->mcount.p, count * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&np->mn.p, count * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&np->ticket.p, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemcpy(np->items.p, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(np->mfirst.p, mf.data(), count * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(np->mcount.p, mc.data(), count * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(np->mn.p, ns, count * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return status_of_b(e);
+    // capture ticket reset + persistent kernel + finalize into a graph
+    cudaStream_t cs = nullptr;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return status_of_b(e);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    int rc = PERM_OK;
+    if (e == cudaSuccess) {
+      rc = enqueue_batch(ptrs, (BatchItem*)np->items.p, np->nitems, (double*)np->partials.p, (int*)np->mfirst.p,
+                         (int*)np->mcount.p, (int*)np->mn.p, count, (unsigned int*)np->ticket.p, out, status, cs);
+      cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+      if (rc == PERM_OK && e2 != cudaSuccess) rc = status_of_b(e2);
+    } else {
+      rc = status_of_b(e);
+    }
+    cudaStreamDestroy(cs);
+    if (rc == PERM_OK) {
+      e = cudaGraphInstantiate(&np->exec, graph, 0);
+      if (e != cudaSuccess) rc = status_of_b(e);
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (rc) return rc;
+    g_plans.push_front(std::move(np));
+    while (g_plans.size() > kMaxPlans) g_plans.pop_back();
+    plan = g_plans.front().get();
+  }
+  return status_of_b(cudaGraphLaunch(plan->exec, s));
+}
+
+}  // extern "C"
+
+namespace perm {
+
+void batch_release_plans() {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  g_plans.clear();
+}
+
+}  // namespace perm

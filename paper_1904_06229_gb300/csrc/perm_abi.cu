@@ -1,0 +1,326 @@
+// C ABI of libperm.so (declarations and contracts in include/perm.h).
+//
+// Host side only marshals: validates arguments, stages host buffers through
+// stream-ordered scratch, splits long code ranges into bounded launches, and
+// enqueues the kernels.  Every arithmetic step of the permanent runs in the
+// CUDA kernels of this library.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <thread>
+
+#include "dd.cuh"
+#include "perm.h"
+#include "perm_internal.h"
+
+namespace perm {
+
+// ---- fixed-order reduction of per-block dd partials (App. A "permanent":
+// S = 2 (-1)^n sum_k S_k with the partials kept in an array, Sec. 2.B) ----
+constexpr int kFinThreads = 256;
+
+__global__ void __launch_bounds__(kFinThreads) k_finalize(const double* __restrict__ partials, int nparts, int cplx,
+                                                          int n, int mode, double* __restrict__ out) {
+  __shared__ dd sRed[2 * (kFinThreads / 32)];
+  const int stride = cplx ? 4 : 2;
+  dd ar{0.0, 0.0}, ai{0.0, 0.0};
+  for (int k = threadIdx.x; k < nparts; k += kFinThreads) {
+    const double* p = partials + (size_t)k * stride;
+    ar = dd_add(ar, dd{p[0], p[1]});
+    if (cplx) ai = dd_add(ai, dd{p[2], p[3]});
+  }
+  ar = dd_warp_sum(ar);
+  ai = dd_warp_sum(ai);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sRed[2 * warp] = ar;
+    sRed[2 * warp + 1] = ai;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    dd tr = sRed[0], ti = sRed[1];
+    for (int w = 1; w < kFinThreads / 32; ++w) {
+      tr = dd_add(tr, sRed[2 * w]);
+      ti = dd_add(ti, sRed[2 * w + 1]);
+    }
+    if (mode == 0) {
+      // per = 2 (-1)^(n-1) * sum ; scaling by +-2 is exact
+      const double s = ((n - 1) & 1) ? -2.0 : 2.0;
+      out[0] = s * __dadd_rn(tr.hi, tr.lo);
+      if (cplx) out[1] = s * __dadd_rn(ti.hi, ti.lo);
+    } else {
+      out[0] = tr.hi;
+      out[1] = tr.lo;
+      if (cplx) {
+        out[2] = ti.hi;
+        out[3] = ti.lo;
+      }
+    }
+  }
+}
+
+cudaError_t finalize_launch(const double* partials, int nparts, bool cplx, int n, int mode, double* out,
+                            cudaStream_t stream) {
+  k_finalize<<<1, kFinThreads, 0, stream>>>(partials, nparts, cplx ? 1 : 0, n, mode, out);
+  return cudaGetLastError();
+}
+
+int device_status_word(int dev, int** out) {
+  static std::mutex mu;
+  static int* words[64] = {nullptr};
+  if (dev < 0 || dev >= 64) return -3;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!words[dev]) {
+    int* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sizeof(int));
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? -6 : -3;
+    e = cudaMemset(p, 0, sizeof(int));
+    if (e != cudaSuccess) {
+      cudaFree(p);
+      return -3;
+    }
+    words[dev] = p;
+  }
+  *out = words[dev];
+  return 0;
+}
+
+int walk_resident_blocks(int n, bool cplx, ProductMode mode) {
+  if (mode == kProdF64) {
+    if (cplx) return n <= 32 ? walk_blocks_c128_f64_lo(n) : walk_blocks_c128_f64_hi(n);
+    return walk_blocks_r64_f64(n);
+  }
+  return cplx ? walk_blocks_c128_f32(n) : walk_blocks_r64_f32(n);
+}
+
+cudaError_t walk_launch(bool cplx, ProductMode mode, const WalkArgs& a) {
+  if (mode == kProdF64) {
+    if (cplx) return a.n <= 32 ? walk_launch_c128_f64_lo(a) : walk_launch_c128_f64_hi(a);
+    return walk_launch_r64_f64(a);
+  }
+  return cplx ? walk_launch_c128_f32(a) : walk_launch_r64_f32(a);
+}
+
+}  // namespace perm
+
+using namespace perm;
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+
+// Codes per launch: bounds each kernel to seconds at n ~ 40-48 on this part.
+constexpr uint64_t kCodesPerLaunch = 1ull << 34;
+// Minimum codes per thread before more threads are worth their seeding cost.
+constexpr uint64_t kMinCodesPerThread = 16;
+
+int status_of(cudaError_t e) {
+  if (e == cudaSuccess) return PERM_OK;
+  if (e == cudaErrorMemoryAllocation) return PERM_ENOMEM;
+  return PERM_ECUDA;
+}
+
+int current_device(int* dev) {
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count < 1) {
+    cudaGetLastError();
+    return PERM_ECUDA;
+  }
+  if (cudaGetDevice(dev) != cudaSuccess || *dev < 0 || *dev >= kMaxDevices) return PERM_ECUDA;
+  return PERM_OK;
+}
+
+// True when p is memory the device can read directly (device or managed).
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Scratch carved from one stream-ordered allocation.
+struct Scratch {
+  char* base = nullptr;
+  cudaStream_t s = nullptr;
+  ~Scratch() {
+    if (base) cudaFreeAsync(base, s);
+  }
+  int alloc(size_t bytes, cudaStream_t stream) {
+    s = stream;
+    cudaError_t e = cudaMallocAsync((void**)&base, bytes ? bytes : 256, stream);
+    if (e != cudaSuccess) {
+      base = nullptr;
+      cudaGetLastError();
+      return status_of(e);
+    }
+    return PERM_OK;
+  }
+};
+
+// Shared driver of every floating-point walk entry point.
+//   final_mode 0: out = permanent (1 or 2 doubles); 1: out = dd partial.
+int run_walk(bool cplx, ProductMode pm, const double* A, int n, uint64_t first, uint64_t count, int final_mode,
+             double* out, void* stream_) {
+  if (!A || !out) return PERM_ENULL;
+  if (n < 1 || n > PERM_NMAX) return PERM_EINVAL;
+  const uint64_t total = 1ull << (n - 1);
+  if (first > total || count > total - first) return PERM_EINVAL;
+  int dev = 0;
+  int rc = current_device(&dev);
+  if (rc) return rc;
+  int* status = nullptr;
+  rc = device_status_word(dev, &status);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream_;
+
+  const int E = cplx ? 2 : 1;
+  const size_t bytesA = (size_t)n * n * E * sizeof(double);
+  const int out_doubles = final_mode == 0 ? E : 2 * E;
+  const bool a_dev = is_device_ptr(A);
+  const bool o_dev = is_device_ptr(out);
+
+  int resident = walk_resident_blocks(n, cplx, pm);
+  if (resident < 1) {
+    cudaGetLastError();
+    return PERM_ECUDA;
+  }
+  uint64_t want = (count + kMinCodesPerThread * kWalkThreads - 1) / (kMinCodesPerThread * kWalkThreads);
+  int blocks = (int)(want < 1 ? 1 : (want > (uint64_t)resident ? (uint64_t)resident : want));
+
+  const size_t offA = 0, szA = a_dev ? 0 : align256(bytesA);
+  const size_t offP = offA + szA, szP = align256((size_t)blocks * 2 * E * sizeof(double));
+  const size_t offO = offP + szP, szO = o_dev ? 0 : align256(out_doubles * sizeof(double));
+  Scratch scr;
+  rc = scr.alloc(offO + szO, s);
+  if (rc) return rc;
+  const double* dA = A;
+  if (!a_dev) {
+    double* d = (double*)(scr.base + offA);
+    cudaError_t e = cudaMemcpyAsync(d, A, bytesA, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return status_of(e);
+    dA = d;
+  }
+  double* partials = (double*)(scr.base + offP);
+  double* dOut = o_dev ? out : (double*)(scr.base + offO);
+
+  uint64_t done = 0;
+  do {
+    const uint64_t len = (count - done) < kCodesPerLaunch ? (count - done) : kCodesPerLaunch;
+    WalkArgs a{dA, n, first + done, len, partials, blocks, done > 0 ? 1 : 0, status, s};
+    cudaError_t e = walk_launch(cplx, pm, a);
+    if (e != cudaSuccess) return status_of(e);
+    done += len;
+  } while (done < count);
+
+  cudaError_t e = finalize_launch(partials, blocks, cplx, n, final_mode, dOut, s);
+  if (e != cudaSuccess) return status_of(e);
+  if (!o_dev) {
+    e = cudaMemcpyAsync(out, dOut, out_doubles * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return status_of(e);
+  }
+  return PERM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int perm_c128(const double* A, int n, double* out, void* stream) {
+  if (n < 1 || n > PERM_NMAX) return (A && out) ? PERM_EINVAL : PERM_ENULL;
+  return run_walk(true, kProdF64, A, n, 0, 1ull << (n - 1), 0, out, stream);
+}
+
+int perm_f64(const double* A, int n, double* out, void* stream) {
+  if (n < 1 || n > PERM_NMAX) return (A && out) ? PERM_EINVAL : PERM_ENULL;
+  return run_walk(false, kProdF64, A, n, 0, 1ull << (n - 1), 0, out, stream);
+}
+
+int perm_c128_range(const double* A, int n, uint64_t first, uint64_t count, double* partial_dd, void* stream) {
+  return run_walk(true, kProdF64, A, n, first, count, 1, partial_dd, stream);
+}
+
+int perm_f64_range(const double* A, int n, uint64_t first, uint64_t count, double* partial_dd, void* stream) {
+  return run_walk(false, kProdF64, A, n, first, count, 1, partial_dd, stream);
+}
+
+int perm_c128_f32p(const double* A, int n, double* out, void* stream) {
+  if (n < 1 || n > PERM_NMAX) return (A && out) ? PERM_EINVAL : PERM_ENULL;
+  return run_walk(true, kProdF32, A, n, 0, 1ull << (n - 1), 0, out, stream);
+}
+
+int perm_f64_f32p(const double* A, int n, double* out, void* stream) {
+  if (n < 1 || n > PERM_NMAX) return (A && out) ? PERM_EINVAL : PERM_ENULL;
+  return run_walk(false, kProdF32, A, n, 0, 1ull << (n - 1), 0, out, stream);
+}
+
+int perm_last_status(void* stream) {
+  int dev = 0;
+  int rc = current_device(&dev);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  double limit = 86400.0;
+  if (const char* env = std::getenv("PERM_TIMEOUT_S")) {
+    double v = std::atof(env);
+    if (v > 0) limit = v;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t q = cudaStreamQuery(s);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) return status_of(q);
+    double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > limit) return PERM_ETIMEOUT;
+    std::this_thread::sleep_for(std::chrono::microseconds(200));
+  }
+  int* word = nullptr;
+  rc = device_status_word(dev, &word);
+  if (rc) return rc;
+  int h = 0;
+  cudaError_t e = cudaMemcpy(&h, word, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return status_of(e);
+  if (h) {
+    e = cudaMemset(word, 0, sizeof(int));
+    if (e != cudaSuccess) return status_of(e);
+  }
+  if (h & kStatusNonFinite) return PERM_ENONFINITE;
+  return PERM_OK;
+}
+
+const char* perm_status_string(int st) {
+  switch (st) {
+    case PERM_OK: return "PERM_OK";
+    case PERM_EINVAL: return "PERM_EINVAL: order or range out of bounds";
+    case PERM_ENULL: return "PERM_ENULL: null pointer";
+    case PERM_ECUDA: return "PERM_ECUDA: CUDA runtime error or no device";
+    case PERM_ENONFINITE: return "PERM_ENONFINITE: non-finite input entry";
+    case PERM_ETIMEOUT: return "PERM_ETIMEOUT: stream did not finish in time";
+    case PERM_ENOMEM: return "PERM_ENOMEM: scratch allocation failed";
+    case PERM_EPRIME: return "PERM_EPRIME: invalid modulus";
+    default: return "unknown perm_status";
+  }
+}
+
+void perm_shutdown(void) {
+  batch_release_plans();
+  int cur = -1, ndev = 0;
+  cudaGetDevice(&cur);
+  if (cudaGetDeviceCount(&ndev) == cudaSuccess) {
+    for (int d = 0; d < ndev && d < kMaxDevices; ++d) {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, d) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+    }
+  }
+  if (cur >= 0) cudaSetDevice(cur);
+  cudaGetLastError();
+}
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// Internal host-side interfaces between the C ABI (perm_abi.cu) and the kernel
+// translation units.  Not installed; the public surface is include/perm.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace perm {
+
+// Device status bits (OR-ed into a per-device word by the kernels).
+enum : int { kStatusNonFinite = 1 };
+
+// Threads per block of the Gray-walk kernels.
+constexpr int kWalkThreads = 128;
+
+// Product arithmetic of a walk kernel.
+enum ProductMode : int {
+  kProdF64 = 0,  // FP64 products (Sec. 2.B "double")
+  kProdF32 = 1,  // FP32 significands with integer exponents
+};
+
+struct WalkArgs {
+  const double* A;     // device, row-major (interleaved re/im when complex)
+  int n;               // order
+  uint64_t first;      // first Gray code index of this launch
+  uint64_t count;      // number of codes in this launch
+  double* partials;    // blocks x (4 complex | 2 real) doubles: per-block dd sums
+  int blocks;          // grid size (<= walk_resident_blocks)
+  int accumulate;      // 1: add into partials, 0: overwrite
+  int* status;         // device status word
+  cudaStream_t stream;
+};
+
+// Largest useful grid for one walk launch (resident blocks on the device).
+int walk_resident_blocks(int n, bool cplx, ProductMode mode);
+
+// Launch the Gray-walk kernel for the given order / type / product mode.
+cudaError_t walk_launch(bool cplx, ProductMode mode, const WalkArgs& a);
+
+// Per-order dispatch inside each kernel translation unit.
+cudaError_t walk_launch_c128_f64_lo(const WalkArgs& a);   // n in 1..32
+cudaError_t walk_launch_c128_f64_hi(const WalkArgs& a);   // n in 33..64
+cudaError_t walk_launch_r64_f64(const WalkArgs& a);       // n in 1..64
+cudaError_t walk_launch_c128_f32(const WalkArgs& a);      // n in 1..64
+cudaError_t walk_launch_r64_f32(const WalkArgs& a);       // n in 1..64
+int walk_blocks_c128_f64_lo(int n);
+int walk_blocks_c128_f64_hi(int n);
+int walk_blocks_r64_f64(int n);
+int walk_blocks_c128_f32(int n);
+int walk_blocks_r64_f32(int n);
+
+// Fixed-order reduction of per-block dd partials.
+//   mode 0: out = 2 (-1)^(n-1) * sum, rounded to double(s)  (1 or 2 doubles)
+//   mode 1: out = sum as dd                                    (2 or 4 doubles)
+cudaError_t finalize_launch(const double* partials, int nparts, bool cplx, int n, int mode, double* out,
+                            cudaStream_t stream);
+
+// ---- modular path ----
+struct ModArgs {
+  const int8_t* A;
+  int n;
+  uint64_t p[4];       // moduli
+  uint64_t pinv[4];    // -p^{-1} mod 2^64
+  uint64_t r2[4];      // 2^128 mod p (Montgomery R^2)
+  uint64_t one[4];     // 2^64 mod p (Montgomery form of 1)
+  uint64_t scale[4];   // (-1)^(n-1) / 2^(n-1) mod p, plain form
+  uint64_t* partials;  // blocks x 4 residues (plain form)
+  int blocks;
+  uint64_t* residues;  // device, 4
+  cudaStream_t stream;
+};
+int mod_resident_blocks(int n);
+cudaError_t mod_launch(const ModArgs& a);
+
+// ---- batch path ----
+struct BatchItem {
+  uint32_t matrix;   // index into the matrix list
+  uint32_t n;        // order
+  uint64_t first;    // first code of this item
+  uint64_t count;    // codes in this item (per warp: 32 lanes share it)
+};
+cudaError_t batch_launch(const double* const* ptrs, const BatchItem* items, int nitems, const int* item_offsets,
+                         const int* nmat_items, int count, double* item_partials, unsigned int* ticket,
+                         double* out, int grid, int* status, cudaStream_t stream);
+int batch_resident_blocks();
+
+// Per-device status word (device int, OR-ed by kernels; read and cleared by
+// perm_last_status).  Allocated on first use.
+int device_status_word(int dev, int** out);
+
+// Drop the cached batch graphs and their buffers (perm_shutdown).
+void batch_release_plans();
+
+// ---- peak probe ----
+cudaError_t dfma_probe_launch(double* sink, int blocks, int iters, cudaStream_t stream);
+
+}  // namespace perm

@@ -1,0 +1,275 @@
+"""Python binding of libperm.so (include/perm.h): argument marshalling only.
+
+Each function has the name of the C entry point it calls, takes torch tensors
+(CUDA tensors are passed by device pointer, CPU tensors by host pointer: the
+library copies host buffers itself) and the current CUDA stream, and raises
+`PermError` on a non-zero status.  Nothing here computes any part of a
+permanent; without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libperm.so")
+PERM_NMAX = 64
+
+STATUS = {
+    0: "PERM_OK",
+    -1: "PERM_EINVAL",
+    -2: "PERM_ENULL",
+    -3: "PERM_ECUDA",
+    -4: "PERM_ENONFINITE",
+    -5: "PERM_ETIMEOUT",
+    -6: "PERM_ENOMEM",
+    -7: "PERM_EPRIME",
+}
+
+# every symbol include/perm.h declares
+EXPORTS = [
+    "perm_c128",
+    "perm_f64",
+    "perm_c128_range",
+    "perm_f64_range",
+    "perm_c128_f32p",
+    "perm_f64_f32p",
+    "perm_batch",
+    "perm_batch_autotune",
+    "perm_mod01",
+    "perm_crt",
+    "perm_default_primes",
+    "perm_last_status",
+    "perm_status_string",
+    "perm_fp64_peak",
+    "perm_shutdown",
+]
+
+
+class PermError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({code})")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: Optional[str] = None):
+    """Load libperm.so (once).  Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libperm.so is not built ({p}); run `python -m paper_1904_06229_gb300.build`")
+        lib = ctypes.CDLL(p)
+        vp, i, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64
+        for name, args in {
+            "perm_c128": [vp, i, vp, vp],
+            "perm_f64": [vp, i, vp, vp],
+            "perm_c128_range": [vp, i, u64, u64, vp, vp],
+            "perm_f64_range": [vp, i, u64, u64, vp, vp],
+            "perm_c128_f32p": [vp, i, vp, vp],
+            "perm_f64_f32p": [vp, i, vp, vp],
+            "perm_batch": [vp, vp, i, vp, vp],
+            "perm_batch_autotune": [i, i],
+            "perm_mod01": [vp, i, vp, vp, vp],
+            "perm_crt": [vp, vp, i, vp],
+            "perm_default_primes": [vp],
+            "perm_last_status": [vp],
+            "perm_status_string": [i],
+            "perm_fp64_peak": [vp],
+            "perm_shutdown": [],
+        }.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        lib.perm_status_string.restype = ctypes.c_char_p
+        lib.perm_shutdown.restype = None
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise PermError(rc, where)
+
+
+def _stream(t: Optional[torch.Tensor], stream) -> Optional[int]:
+    if stream is not None:
+        return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+    if t is not None and t.is_cuda:
+        return int(torch.cuda.current_stream(t.device).cuda_stream)
+    if torch.cuda.is_available():
+        return int(torch.cuda.current_stream().cuda_stream)
+    return None
+
+
+def _square(A: torch.Tensor) -> int:
+    if A.dim() != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("A must be a square matrix")
+    return int(A.shape[0])
+
+
+def _dptr(t: torch.Tensor) -> int:
+    return int(t.data_ptr())
+
+
+def _c128(A: torch.Tensor) -> torch.Tensor:
+    if A.dtype != torch.complex128:
+        raise TypeError("complex128 matrix expected")
+    return A.contiguous()
+
+
+def _f64(A: torch.Tensor) -> torch.Tensor:
+    if A.dtype != torch.float64:
+        raise TypeError("float64 matrix expected")
+    return A.contiguous()
+
+
+def _out(out: Optional[torch.Tensor], n: int, like: torch.Tensor, dtype=torch.float64) -> torch.Tensor:
+    if out is None:
+        out = torch.empty(n, dtype=dtype, device=like.device)
+    if out.numel() < n or not out.is_contiguous():
+        raise ValueError("output buffer too small or not contiguous")
+    return out
+
+
+def perm_c128(A: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """per(A) of a complex128 n x n tensor -> float64 tensor [re, im]."""
+    A = _c128(A)
+    n = _square(A)
+    out = _out(out, 2, A)
+    _check(load().perm_c128(_dptr(A), n, _dptr(out), _stream(A, stream)), "perm_c128")
+    return out
+
+
+def perm_f64(A: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """per(A) of a float64 n x n tensor -> float64 tensor [value]."""
+    A = _f64(A)
+    n = _square(A)
+    out = _out(out, 1, A)
+    _check(load().perm_f64(_dptr(A), n, _dptr(out), _stream(A, stream)), "perm_f64")
+    return out
+
+
+def perm_c128_range(A: torch.Tensor, first: int, count: int, out: Optional[torch.Tensor] = None,
+                    stream=None) -> torch.Tensor:
+    """Unscaled Gray-code partial over [first, first+count) -> [re_hi, re_lo, im_hi, im_lo]."""
+    A = _c128(A)
+    n = _square(A)
+    out = _out(out, 4, A)
+    _check(load().perm_c128_range(_dptr(A), n, int(first), int(count), _dptr(out), _stream(A, stream)),
+           "perm_c128_range")
+    return out
+
+
+def perm_f64_range(A: torch.Tensor, first: int, count: int, out: Optional[torch.Tensor] = None,
+                   stream=None) -> torch.Tensor:
+    A = _f64(A)
+    n = _square(A)
+    out = _out(out, 2, A)
+    _check(load().perm_f64_range(_dptr(A), n, int(first), int(count), _dptr(out), _stream(A, stream)),
+           "perm_f64_range")
+    return out
+
+
+def perm_c128_f32p(A: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    A = _c128(A)
+    n = _square(A)
+    out = _out(out, 2, A)
+    _check(load().perm_c128_f32p(_dptr(A), n, _dptr(out), _stream(A, stream)), "perm_c128_f32p")
+    return out
+
+
+def perm_f64_f32p(A: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    A = _f64(A)
+    n = _square(A)
+    out = _out(out, 1, A)
+    _check(load().perm_f64_f32p(_dptr(A), n, _dptr(out), _stream(A, stream)), "perm_f64_f32p")
+    return out
+
+
+def perm_batch(mats: Sequence[torch.Tensor], out: Optional[torch.Tensor] = None, stream=None,
+               ptrs: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Permanents of a list of complex128 CUDA matrices -> (count, 2) float64.
+
+    `ptrs` may pass a prebuilt device int64 tensor of the matrices' addresses."""
+    count = len(mats)
+    if count == 0:
+        raise ValueError("empty batch")
+    dev = mats[0].device
+    ns = (ctypes.c_int * count)(*[_square(m) for m in mats])
+    for m in mats:
+        if m.dtype != torch.complex128 or not m.is_contiguous() or m.device != dev:
+            raise TypeError("contiguous complex128 matrices on one device expected")
+    if ptrs is None:
+        ptrs = torch.tensor([m.data_ptr() for m in mats], dtype=torch.int64).to(dev)
+    if out is None:
+        out = torch.empty((count, 2), dtype=torch.float64, device=dev)
+    _check(load().perm_batch(_dptr(ptrs), ctypes.addressof(ns), count, _dptr(out), _stream(mats[0], stream)),
+           "perm_batch")
+    return out
+
+
+def perm_batch_autotune(n_lo: int, n_hi: int) -> None:
+    _check(load().perm_batch_autotune(int(n_lo), int(n_hi)), "perm_batch_autotune")
+
+
+def perm_default_primes() -> list:
+    buf = (ctypes.c_uint64 * 4)()
+    _check(load().perm_default_primes(ctypes.addressof(buf)), "perm_default_primes")
+    return [int(v) for v in buf]
+
+
+def perm_mod01(A: torch.Tensor, primes: Optional[Sequence[int]] = None, residues: Optional[torch.Tensor] = None,
+               stream=None) -> torch.Tensor:
+    """per(A) mod each of four primes for an int8 n x n tensor -> int64 tensor (4,)."""
+    if A.dtype != torch.int8:
+        raise TypeError("int8 matrix expected")
+    A = A.contiguous()
+    n = _square(A)
+    if primes is None:
+        primes = perm_default_primes()
+    pr = (ctypes.c_uint64 * 4)(*[int(p) for p in primes])
+    residues = _out(residues, 4, A, dtype=torch.int64)
+    _check(load().perm_mod01(_dptr(A), n, ctypes.addressof(pr), _dptr(residues), _stream(A, stream)), "perm_mod01")
+    return residues
+
+
+def perm_crt(residues: Sequence[int], primes: Sequence[int]) -> int:
+    """Signed integer with the given residues (|x| <= P/2), via the library's host CRT."""
+    k = len(primes)
+    r = (ctypes.c_uint64 * k)(*[int(v) for v in residues])
+    p = (ctypes.c_uint64 * k)(*[int(v) for v in primes])
+    out = (ctypes.c_uint64 * 4)()
+    _check(load().perm_crt(ctypes.addressof(r), ctypes.addressof(p), k, ctypes.addressof(out)), "perm_crt")
+    v = sum(int(out[i]) << (64 * i) for i in range(4))
+    return v - (1 << 256) if v >> 255 else v
+
+
+def perm_last_status(stream=None) -> int:
+    """Wait for the stream and return (and clear) the device-side status code."""
+    return int(load().perm_last_status(_stream(None, stream)))
+
+
+def perm_status_string(code: int) -> str:
+    return load().perm_status_string(int(code)).decode()
+
+
+def perm_fp64_peak() -> float:
+    """Measured FP64 DFMA rate of the current device, in Gop/s (lane DFMAs)."""
+    v = ctypes.c_double(0.0)
+    _check(load().perm_fp64_peak(ctypes.addressof(v)), "perm_fp64_peak")
+    return float(v.value)
+
+
+def perm_shutdown() -> None:
+    load().perm_shutdown()

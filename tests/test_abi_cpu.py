@@ -1,0 +1,114 @@
+"""C ABI checks that need no GPU: the library builds and loads, exports every
+symbol include/perm.h declares, and its host-only helpers (prime search,
+Chinese remaindering, status strings) behave; compute calls without a device
+fail with PERM_ECUDA instead of falling back to the CPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1904_06229_gb300 import build, perm
+
+    build.build()
+    return perm.load()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "perm.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(perm_\w+)\s*\(", txt, re.M)))
+
+
+def test_header_matches_binding_list():
+    from paper_1904_06229_gb300 import perm
+
+    assert _declared() == sorted(perm.EXPORTS)
+
+
+def test_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_no_cuda_runtime_dependency(lib):
+    from paper_1904_06229_gb300 import perm
+
+    # the runtime is linked statically; only the driver is needed at run time
+    maps = open("/proc/self/maps").read()
+    assert perm.LIB_PATH in maps
+
+
+def test_default_primes_match_oracle(lib):
+    from oracle import oracle as O
+    from paper_1904_06229_gb300 import perm
+
+    assert perm.perm_default_primes() == O.default_primes()
+
+
+def test_crt_host(lib):
+    from oracle import oracle as O
+    from paper_1904_06229_gb300 import perm
+
+    ps = perm.perm_default_primes()
+    for v in (0, 1, -1, 12345678901234567890, -(3**150), (1 << 240) - 7):
+        assert perm.perm_crt([v % p for p in ps], ps) == v
+        assert perm.perm_crt([v % p for p in ps], ps) == O.crt([v % p for p in ps], ps)
+    # fewer moduli
+    assert perm.perm_crt([5 % ps[0]], ps[:1]) == 5
+    assert perm.perm_crt([(-5) % ps[0], (-5) % ps[1]], ps[:2]) == -5
+
+
+def test_crt_errors(lib):
+    from paper_1904_06229_gb300 import perm
+
+    with pytest.raises(perm.PermError) as e:
+        perm.perm_crt([1, 2], [7, 7])
+    assert e.value.code == -7
+    with pytest.raises(perm.PermError) as e:
+        perm.perm_crt([9], [7])
+    assert e.value.code == -1
+
+
+def test_status_strings(lib):
+    from paper_1904_06229_gb300 import perm
+
+    for code, name in perm.STATUS.items():
+        assert perm.perm_status_string(code).startswith(name)
+
+
+def test_argument_errors_before_device(lib):
+    """Argument errors are reported before any CUDA call."""
+    vp = ctypes.c_void_p
+    buf = (ctypes.c_double * 8)()
+    a = ctypes.addressof(buf)
+    assert lib.perm_c128(None, 3, a, None) == -2
+    assert lib.perm_c128(a, 0, a, None) == -1
+    assert lib.perm_c128(a, 65, a, None) == -1
+    assert lib.perm_f64(a, -1, a, None) == -1
+    assert lib.perm_c128_range(a, 3, 4, 1, a, None) == -1  # past 2^(n-1)
+    assert lib.perm_c128_range(a, 3, 0, 5, a, None) == -1
+    pr = (ctypes.c_uint64 * 4)(7, 11, 13, 13)
+    assert lib.perm_mod01(a, 3, ctypes.addressof(pr), a, None) == -7
+    pr = (ctypes.c_uint64 * 4)(7, 11, 13, 1 << 62)
+    assert lib.perm_mod01(a, 3, ctypes.addressof(pr), a, None) == -7
+    pr = (ctypes.c_uint64 * 4)(7, 11, 13, 16)
+    assert lib.perm_mod01(a, 3, ctypes.addressof(pr), a, None) == -7
+
+
+def test_no_cpu_fallback_without_device(lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("device present")
+    buf = (ctypes.c_double * 8)(1, 0, 0, 0, 0, 0, 0, 0)
+    out = (ctypes.c_double * 2)()
+    assert lib.perm_c128(ctypes.addressof(buf), 1, ctypes.addressof(out), None) == -3
+    assert lib.perm_f64(ctypes.addressof(buf), 1, ctypes.addressof(out), None) == -3
+    assert lib.perm_last_status(None) == -3
+    v = ctypes.c_double()
+    assert lib.perm_fp64_peak(ctypes.addressof(v)) == -3

@@ -1,0 +1,258 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, on the
+same seeded inputs.
+
+Tolerances.  FP64 results must agree with the oracle to 1e-10 relative
+(|got - ref| / |ref|); the walk's own error at these sizes is far smaller,
+and the closed-form cases with huge cancellation (J_n, J - I) use the
+a-posteriori bound 64 n u Sigma|t| from the oracle's sum of term magnitudes.
+Integer / modular results must be bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_1904_06229_gb300 import perm as P
+from paper_1904_06229_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+U64 = 2.0 ** -53
+REL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    P.load()
+    yield
+    torch.cuda.synchronize()
+
+
+def dev_c(A):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(A, dtype=np.complex128))).cuda()
+
+
+def dev_r(A):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(A, dtype=np.float64))).cuda()
+
+
+def gpu_c128(A):
+    out = P.perm_c128(dev_c(A))
+    assert P.perm_last_status() == 0
+    o = out.cpu().numpy()
+    return complex(o[0], o[1])
+
+
+def gpu_f64(A):
+    out = P.perm_f64(dev_r(A))
+    assert P.perm_last_status() == 0
+    return float(out.cpu().numpy()[0])
+
+
+def oracle_c(A):
+    r = O.per(A)
+    return complex(float(r[0]), float(r[1])), float(r[2])
+
+
+def rel_err(got, ref):
+    return abs(got - ref) / abs(ref) if ref != 0 else abs(got)
+
+
+# ---------------------------------------------------------------- complex
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 8, 9, 11, 13, 16, 17, 20, 23, 24])
+def test_c128_vs_oracle_gaussian(n):
+    A = W.complex_gaussian(n, 500 + n)
+    ref, asum = oracle_c(A)
+    got = gpu_c128(A)
+    assert rel_err(got, ref) <= REL, (got, ref)
+
+
+@pytest.mark.parametrize("n", [6, 12, 18, 22])
+def test_c128_vs_oracle_haar(n):
+    A = W.haar_submatrix(n, n * n, 1000 + n)
+    ref, _ = oracle_c(A)
+    assert rel_err(gpu_c128(A), ref) <= REL
+
+
+def test_c128_config_n20_seed0():
+    """one 20x20 complex128 matrix, entries N(0,1/2) + i N(0,1/2), seed 0."""
+    A = W.complex_gaussian(20, 0)
+    ref, asum = oracle_c(A)
+    got = gpu_c128(A)
+    err = rel_err(got, ref)
+    print(f"n=20 seed0: gpu={got!r} oracle={ref!r} rel={err:.3e} kappa={asum / abs(ref):.3e}")
+    assert err <= REL
+
+
+# ---------------------------------------------------------------- real
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 10, 15, 19, 24])
+def test_f64_vs_oracle(n):
+    A = W.real_gaussian(n, 700 + n)
+    ref, _ = oracle_c(A)
+    got = gpu_f64(A)
+    assert abs(got - ref.real) <= REL * abs(ref.real)
+
+
+# ---------------------------------------------------------- closed forms
+@pytest.mark.parametrize("n", [1, 2, 5, 10, 16, 20, 24])
+def test_all_ones_factorial(n):
+    ref = math.factorial(n)
+    _, asum = oracle_c(np.ones((n, n)))
+    tol = max(REL * ref, 64 * n * U64 * asum)
+    assert abs(gpu_f64(np.ones((n, n))) - ref) <= tol
+    assert abs(gpu_c128(np.ones((n, n)) * (1 + 0j)) - ref) <= tol
+
+
+@pytest.mark.parametrize("n", [3, 8, 15, 21])
+def test_derangements_and_identity(n):
+    D = [1, 0]
+    for k in range(2, n + 1):
+        D.append((k - 1) * (D[-1] + D[-2]))
+    J = np.ones((n, n)) - np.eye(n)
+    _, asum = oracle_c(J)
+    assert abs(gpu_f64(J) - D[n]) <= max(REL * D[n], 64 * n * U64 * asum)
+    assert gpu_f64(np.eye(n)) == 1.0
+    Pm = np.eye(n)[np.random.default_rng(n).permutation(n)]
+    assert gpu_c128(Pm) == 1.0
+
+
+@pytest.mark.parametrize("n", [10, 19])
+def test_rank_one(n):
+    rng = np.random.default_rng(n)
+    u = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    ref = math.factorial(n) * np.prod(u) * np.prod(v)
+    _, asum = oracle_c(np.outer(u, v))
+    assert abs(gpu_c128(np.outer(u, v)) - ref) <= max(REL * abs(ref), 64 * n * U64 * asum)
+
+
+def test_block_diagonal_n32():
+    """per(diag(B, C)) = per(B) per(C): a full-size closed-form pin."""
+    B = W.haar_submatrix(16, 256, 31)
+    C = W.complex_gaussian(16, 32)
+    M = np.zeros((32, 32), dtype=complex)
+    M[:16, :16] = B
+    M[16:, 16:] = C
+    ref = oracle_c(B)[0] * oracle_c(C)[0]
+    got = gpu_c128(M)
+    assert rel_err(got, ref) <= REL, (got, ref)
+
+
+def test_invariances_n26():
+    A = W.haar_submatrix(26, 676, 26)
+    p0 = gpu_c128(A)
+    rng = np.random.default_rng(3)
+    for B in (A.T, A[rng.permutation(26)], A[:, rng.permutation(26)]):
+        assert rel_err(gpu_c128(B), p0) <= REL
+
+
+# ---------------------------------------------------------------- ranges
+def _partial(A, first, count):
+    o = P.perm_c128_range(dev_c(A), first, count).cpu().numpy()
+    return complex(o[0] + o[1], o[2] + o[3])
+
+
+@pytest.mark.parametrize("n", [3, 9, 16])
+def test_range_every_single_code(n):
+    A = W.complex_gaussian(n, 40 + n)
+    N = 1 << (n - 1)
+    idx = range(N) if N <= 64 else list(range(8)) + [N // 2 - 1, N // 2, N - 2, N - 1]
+    for r in idx:
+        g = O.glynn_partial(A, r, 1)
+        ref = complex(float(g[0]), float(g[1]))
+        got = _partial(A, r, 1)
+        assert abs(got - ref) <= 1e-13 * max(1.0, abs(ref)), (r, got, ref)
+
+
+@pytest.mark.parametrize("first,count", [(0, 0), (0, 1), (5, 3), (1000, 4097), (4095, 8193), (123457, 65536),
+                                         ((1 << 21) - 3000, 3000)])
+def test_range_ragged_n22(first, count):
+    A = W.complex_gaussian(22, 9)
+    g = O.glynn_partial(A, first, count)
+    ref = complex(float(g[0]), float(g[1]))
+    got = _partial(A, first, count)
+    tol = 1e-12 * max(abs(ref), float(g[2]) * 1e-3, 1e-300)
+    assert abs(got - ref) <= tol, (got, ref)
+
+
+def test_range_partition_equals_full():
+    n = 21
+    A = W.haar_submatrix(n, n * n, 5)
+    N = 1 << (n - 1)
+    cuts = [0, 17, 4096, 99999, N // 2, N - 1, N]
+    s = sum(_partial(A, a, b - a) for a, b in zip(cuts[:-1], cuts[1:]))
+    full = gpu_c128(A)
+    assert rel_err(2 * (-1) ** (n - 1) * s, full) <= 1e-13
+
+
+@pytest.mark.parametrize("n", [40, 48])
+def test_range_slices_full_size_haar(n):
+    """The benchmark's matrices (Haar S(n^2, n)) on sampled code slices spread
+    over the whole range, each in a full-grid launch, against the oracle's
+    walk over the same slice."""
+    A = W.haar_submatrix(n, n * n, 1000 + n)
+    N = 1 << (n - 1)
+    count = 1 << 18
+    for first in (0, N // 3 - 12345, N - count):
+        g = O.glynn_partial_parts(A, first, count, parts=32)
+        ref = complex(float(g[0]), float(g[1]))
+        got = _partial(A, first, count)
+        tol = max(REL * abs(ref), 64 * n * U64 * float(g[2]))
+        assert abs(got - ref) <= tol, (first, got, ref, float(g[2]))
+
+
+def test_range_long_multi_launch():
+    """More codes than one launch carries (2^34): exercises the launch split."""
+    n = 36
+    A = W.haar_submatrix(n, n * n, 77)
+    first, count = 12345, (1 << 34) + 1000
+    s_whole = _partial(A, first, count)
+    s_parts = _partial(A, first, 1 << 33) + _partial(A, first + (1 << 33), count - (1 << 33))
+    assert abs(s_whole - s_parts) <= 1e-12 * abs(s_whole)
+
+
+# ---------------------------------------------------------------- edge cases
+def test_errors_and_status():
+    A = dev_c(W.complex_gaussian(4, 1))
+    with pytest.raises(P.PermError) as e:
+        P.perm_c128(dev_c(np.zeros((0, 0))))
+    assert e.value.code == -1
+    with pytest.raises(P.PermError) as e:
+        P.perm_c128_range(A, 7, 2)
+    assert e.value.code == -1
+    B = W.complex_gaussian(5, 2)
+    B[2, 3] = np.nan
+    out = P.perm_c128(dev_c(B)).cpu().numpy()
+    assert np.isnan(out).any()
+    assert P.perm_last_status() == -4
+    assert P.perm_last_status() == 0  # cleared
+
+
+def test_host_buffers_match_device():
+    A = W.complex_gaussian(14, 3)
+    host = P.perm_c128(torch.from_numpy(A.astype(np.complex128)))
+    torch.cuda.synchronize()
+    assert host.device.type == "cpu"
+    devv = P.perm_c128(dev_c(A)).cpu()
+    assert torch.equal(host, devv)
+
+
+def test_deterministic_repeat():
+    A = dev_c(W.haar_submatrix(27, 729, 8))
+    a = P.perm_c128(A).cpu()
+    b = P.perm_c128(A).cpu()
+    assert torch.equal(a, b)
+
+
+def test_n64_range_edges():
+    """n = PERM_NMAX: the last codes of the 2^63-code range, and the first."""
+    n = 64
+    A = W.complex_gaussian(n, 64) * 0.5
+    N = 1 << 63
+    for first, count in ((N - 40, 40), (0, 40)):
+        g = O.glynn_partial(A, first, count)
+        ref = complex(float(g[0]), float(g[1]))
+        got = _partial(A, first, count)
+        assert abs(got - ref) <= max(1e-12 * abs(ref), 1e-12 * float(g[2]))
