@@ -45,7 +45,7 @@ def workload_matrix():
 def config_dict(world):
     return {
         "workload": f"n={N_ORDER} complex128 Haar S({N_ORDER * N_ORDER},{N_ORDER}) seed {SEED}; "
-                    f"one step = one 2^33-code Gray slice of its permanent (2^39 codes in all)",
+                    f"one step = one {CODES_PER_STEP}-code Gray slice of its permanent (2^39 codes in all)",
         "n": N_ORDER,
         "codes_per_step": CODES_PER_STEP,
         "matrix_bytes": 16 * N_ORDER * N_ORDER,
@@ -343,9 +343,15 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--batch-sample", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--codes-log2", type=int, default=33,
+                    help="codes per step (2^k); smaller values make a short case for profiling")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    global CODES_PER_STEP
+    if not 10 <= args.codes_log2 <= 38:
+        raise SystemExit("--codes-log2 must be in 10..38")
+    CODES_PER_STEP = 1 << args.codes_log2
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -245,8 +245,8 @@ uint64_t pow_r_mod(uint64_t p, int k) {  // R^k mod p, R = 2^64
 
 extern "C" int perm_mod01(const int8_t* A, int n, const uint64_t* primes, uint64_t* residues, void* stream) {
   using namespace perm;
-  if (!A || !primes || !residues) return PERM_ENULL;
   if (n < 1 || n > PERM_NMAX) return PERM_EINVAL;
+  if (!A || !primes || !residues) return PERM_ENULL;
   int rc = check_moduli(primes, 4);
   if (rc) return rc;
   int count_dev = 0, dev = 0;

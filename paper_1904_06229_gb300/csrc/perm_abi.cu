@@ -170,8 +170,8 @@ struct Scratch {
 //   final_mode 0: out = permanent (1 or 2 doubles); 1: out = dd partial.
 int run_walk(bool cplx, ProductMode pm, const double* A, int n, uint64_t first, uint64_t count, int final_mode,
              double* out, void* stream_) {
-  if (!A || !out) return PERM_ENULL;
   if (n < 1 || n > PERM_NMAX) return PERM_EINVAL;
+  if (!A || !out) return PERM_ENULL;
   const uint64_t total = 1ull << (n - 1);
   if (first > total || count > total - first) return PERM_EINVAL;
   int dev = 0;
@@ -235,12 +235,12 @@ int run_walk(bool cplx, ProductMode pm, const double* A, int n, uint64_t first, 
 extern "C" {
 
 int perm_c128(const double* A, int n, double* out, void* stream) {
-  if (n < 1 || n > PERM_NMAX) return (A && out) ? PERM_EINVAL : PERM_ENULL;
+  if (n < 1 || n > PERM_NMAX) return PERM_EINVAL;
   return run_walk(true, kProdF64, A, n, 0, 1ull << (n - 1), 0, out, stream);
 }
 
 int perm_f64(const double* A, int n, double* out, void* stream) {
-  if (n < 1 || n > PERM_NMAX) return (A && out) ? PERM_EINVAL : PERM_ENULL;
+  if (n < 1 || n > PERM_NMAX) return PERM_EINVAL;
   return run_walk(false, kProdF64, A, n, 0, 1ull << (n - 1), 0, out, stream);
 }
 
@@ -253,12 +253,12 @@ int perm_f64_range(const double* A, int n, uint64_t first, uint64_t count, doubl
 }
 
 int perm_c128_f32p(const double* A, int n, double* out, void* stream) {
-  if (n < 1 || n > PERM_NMAX) return (A && out) ? PERM_EINVAL : PERM_ENULL;
+  if (n < 1 || n > PERM_NMAX) return PERM_EINVAL;
   return run_walk(true, kProdF32, A, n, 0, 1ull << (n - 1), 0, out, stream);
 }
 
 int perm_f64_f32p(const double* A, int n, double* out, void* stream) {
-  if (n < 1 || n > PERM_NMAX) return (A && out) ? PERM_EINVAL : PERM_ENULL;
+  if (n < 1 || n > PERM_NMAX) return PERM_EINVAL;
   return run_walk(false, kProdF32, A, n, 0, 1ull << (n - 1), 0, out, stream);
 }
 
