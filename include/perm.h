@@ -81,6 +81,25 @@ int perm_f64(const double* A, int n, double* out, void* stream);
 int perm_c128_range(const double* A, int n, uint64_t first, uint64_t count, double* partial_dd, void* stream);
 int perm_f64_range(const double* A, int n, uint64_t first, uint64_t count, double* partial_dd, void* stream);
 
+/* ---- Allocation-free variant of perm_c128 (the paper has no counterpart:
+ * this exists for callers that cannot allocate device memory) ----
+ * Same result as perm_c128 (same kernels, same summation order), for callers
+ * that must not call cudaMalloc / cudaMallocAsync -- for example code running
+ * in a host callback, inside an allocator hook, under a budget that forbids
+ * allocation after start-up, or in a latency-bound loop.  The per-block
+ * partial sums live in a fixed 65,792-byte static device array inside the
+ * library (2048 block slots of 32 bytes plus a 256-byte status word), held by
+ * every GPU that loads the library until the process exits; a launch never
+ * uses more than 2048 blocks.  A and out must be DEVICE (or managed) memory:
+ * host pointers are rejected with PERM_EINVAL, as are n < 1 and n > PERM_NMAX;
+ * NULL gives PERM_ENULL.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) and must come before any stream
+ * capture.  All calls on a device share the array: calls whose kernels
+ * overlap on the GPU (e.g. on two streams) race and must be serialised.  A
+ * non-finite input gives a NaN result; perm_last_status does not report it
+ * for this entry point.  No allocation of any kind is made. */
+int perm_c128_noalloc(const double* A, int n, double* out, void* stream);
+
 /* ---- FP32-product variant (precision schemes of Sec. 2.B: product precision
  * chosen apart from sum precision) ----
  * Row sums and the accumulation as in perm_c128 / perm_f64 (FP64, double-

@@ -33,6 +33,7 @@ SOURCES = [
     "batch.cu",
     "perm_abi.cu",
     "peak.cu",
+    "noalloc.cu",
     "host_modular.cpp",
 ]
 

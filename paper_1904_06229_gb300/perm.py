@@ -38,6 +38,7 @@ EXPORTS = [
     "perm_f64_range",
     "perm_c128_f32p",
     "perm_f64_f32p",
+    "perm_c128_noalloc",
     "perm_batch",
     "perm_batch_autotune",
     "perm_mod01",
@@ -78,6 +79,7 @@ def load(path: Optional[str] = None):
             "perm_f64_range": [vp, i, u64, u64, vp, vp],
             "perm_c128_f32p": [vp, i, vp, vp],
             "perm_f64_f32p": [vp, i, vp, vp],
+            "perm_c128_noalloc": [vp, i, vp, vp],
             "perm_batch": [vp, vp, i, vp, vp],
             "perm_batch_autotune": [i, i],
             "perm_mod01": [vp, i, vp, vp, vp],
@@ -194,6 +196,16 @@ def perm_f64_f32p(A: torch.Tensor, out: Optional[torch.Tensor] = None, stream=No
     n = _square(A)
     out = _out(out, 1, A)
     _check(load().perm_f64_f32p(_dptr(A), n, _dptr(out), _stream(A, stream)), "perm_f64_f32p")
+    return out
+
+
+def perm_c128_noalloc(A: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+    """perm_c128 without any device allocation: A and out must be CUDA
+    tensors (complex128 n x n, float64 (2,)).  Calls that overlap on the GPU
+    share one scratch array and must be serialised."""
+    A = _c128(A)
+    n = _square(A)
+    _check(load().perm_c128_noalloc(_dptr(A), n, _dptr(out), _stream(A, stream)), "perm_c128_noalloc")
     return out
 
 
