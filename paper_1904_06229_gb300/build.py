@@ -29,6 +29,11 @@ SOURCES = [
     "walk_r64_f64.cu",
     "walk_c128_f32.cu",
     "walk_r64_f32.cu",
+    "walk_fx_c128_f64_lo.cu",
+    "walk_fx_c128_f64_hi.cu",
+    "walk_fx_r64_f64.cu",
+    "walk_fx_c128_f32.cu",
+    "walk_fx_r64_f32.cu",
     "glynn_mod.cu",
     "batch.cu",
     "perm_abi.cu",

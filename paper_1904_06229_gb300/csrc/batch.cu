@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "glynn_walk.cuh"
+#include "glynn_walk_fx.cuh"
 #include "perm.h"
 #include "perm_internal.h"
 
@@ -35,28 +36,37 @@ namespace perm {
 constexpr int kBatchNMax = 32;
 constexpr int kBatchThreads = 128;
 constexpr int kBatchWarps = kBatchThreads / 32;
-constexpr size_t kBatchSlot = (size_t)kBatchNMax * kBatchNMax + kBatchNMax;  // double2 per warp slot
-constexpr size_t kBatchSmem = kBatchSlot * kBatchWarps * sizeof(double2);
+// Per-warp shared slot (16-byte units): the FP64-row walk keeps A (n^2) and
+// w0 (n); the fixed-point walk keeps +2A (n^2), v0 (n) and two int rows.
+constexpr size_t kBatchSlot = (size_t)kBatchNMax * kBatchNMax + kBatchNMax + (2 * kBatchNMax * 4 + 15) / 16;
+constexpr size_t kBatchSmem = kBatchSlot * kBatchWarps * 16;
 
-template <int K>
-__device__ __forceinline__ void batch_walk_case(int n, const double2* sA, const double2* sW0, uint64_t r, uint64_t end,
-                                                dd& accr, dd& acci) {
+template <int K, int ROWS>
+__device__ __forceinline__ void batch_walk_case(int n, double2* slot, uint64_t r, uint64_t end, dd& accr, dd& acci) {
   if constexpr (K <= kBatchNMax) {
     if (n == K) {
-      thread_walk_c128<K, kProdF64>(sA, sW0, r, end, accr, acci);
+      if constexpr (ROWS == kRowsFixed) {
+        const longlong2* sP = reinterpret_cast<const longlong2*>(slot);
+        const longlong2* sV0 = sP + K * K;
+        const int* sEb = reinterpret_cast<const int*>(sV0 + K);
+        thread_walk_c128_fx<K, kProdF64, false>(sP, nullptr, sV0, sEb, r, end, accr, acci);
+      } else {
+        thread_walk_c128<K, kProdF64>(slot, slot + K * K, r, end, accr, acci);
+      }
       return;
     }
-    batch_walk_case<K + 1>(n, sA, sW0, r, end, accr, acci);
+    batch_walk_case<K + 1, ROWS>(n, slot, r, end, accr, acci);
   }
 }
 
+template <int ROWS>
 __global__ void __launch_bounds__(kBatchThreads) k_batch(const double* const* __restrict__ ptrs,
                                                          const BatchItem* __restrict__ items, int nitems,
                                                          double* __restrict__ item_partials,
                                                          unsigned int* __restrict__ ticket, int* __restrict__ status) {
   extern __shared__ __align__(16) double2 bsm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double2* sA = bsm + (size_t)warp * kBatchSlot;
+  double2* slot = bsm + (size_t)warp * kBatchSlot;
   for (;;) {
     unsigned int it = 0;
     if (lane == 0) it = atomicAdd(ticket, 1u);
@@ -65,33 +75,46 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const double* const* __
     const BatchItem item = items[it];
     const int n = (int)item.n;
     const double2* __restrict__ A = reinterpret_cast<const double2*>(ptrs[item.matrix]);
-    double2* sW0 = sA + n * n;
-    // stage column-major (the single-matrix kernel's layout)
-    int bad = 0;
-    for (int idx = lane; idx < n * n; idx += 32) {
-      const int i = idx / n, j = idx - i * n;
-      const double2 v = A[idx];
-      bad |= (not_finite(v.x) || not_finite(v.y)) ? 1 : 0;
-      sA[j * n + i] = v;
-    }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, (int)kStatusNonFinite);
-    __syncwarp();
-    if (lane < n) {
-      double sr = 0.0, si = 0.0;
-      for (int j = 0; j < n; ++j) {
-        sr += sA[j * n + lane].x;
-        si += sA[j * n + lane].y;
+    bool bad = false;
+    if constexpr (ROWS == kRowsFixed) {
+      longlong2* sP = reinterpret_cast<longlong2*>(slot);
+      longlong2* sV0 = sP + n * n;
+      int* sEb = reinterpret_cast<int*>(sV0 + n);
+      bad = fx_stage_warp_c128(A, n, sP, sV0, sEb, sEb + n);
+    } else {
+      // stage column-major (the single-matrix kernel's layout) and w0
+      double2* sA = slot;
+      double2* sW0 = slot + n * n;
+      int b = 0;
+      for (int idx = lane; idx < n * n; idx += 32) {
+        const int i = idx / n, j = idx - i * n;
+        const double2 v = A[idx];
+        b |= (not_finite(v.x) || not_finite(v.y)) ? 1 : 0;
+        sA[j * n + i] = v;
       }
-      const double2 last = sA[(n - 1) * n + lane];
-      sW0[lane] = make_double2(fma(-0.5, sr, last.x), fma(-0.5, si, last.y));
+      bad = __any_sync(0xffffffffu, b) != 0;
+      __syncwarp();
+      if (lane < n) {
+        double sr = 0.0, si = 0.0;
+        for (int j = 0; j < n; ++j) {
+          sr += sA[j * n + lane].x;
+          si += sA[j * n + lane].y;
+        }
+        const double2 last = sA[(n - 1) * n + lane];
+        sW0[lane] = make_double2(fma(-0.5, sr, last.x), fma(-0.5, si, last.y));
+      }
+      __syncwarp();
     }
-    __syncwarp();
+    if (bad && lane == 0) atomicOr(status, (int)kStatusNonFinite);
     // this lane's share of the item ("distribute" over 32 lanes)
     const uint64_t q = item.count / 32, rem = item.count % 32;
     const uint64_t r = item.first + lane * q + ((uint64_t)lane < rem ? lane : rem);
     const uint64_t end = r + q + ((uint64_t)lane < rem ? 1 : 0);
     dd accr{0.0, 0.0}, acci{0.0, 0.0};
-    batch_walk_case<1>(n, sA, sW0, r, end, accr, acci);
+    if (!bad)
+      batch_walk_case<1, ROWS>(n, slot, r, end, accr, acci);
+    else
+      accr = acci = dd{__longlong_as_double(0x7ff8000000000000ll), 0.0};
     accr = dd_warp_sum(accr);
     acci = dd_warp_sum(acci);
     if (lane == 0) {
@@ -123,20 +146,29 @@ __global__ void k_batch_finalize(const double* __restrict__ item_partials, const
   out[2 * k + 1] = s * __dadd_rn(ai.hi, ai.lo);
 }
 
-int batch_resident_blocks() {
+template <int ROWS>
+int batch_resident_blocks_t() {
   static int cached[64] = {0};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
   if (cached[dev]) return cached[dev];
-  if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_batch<ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) !=
+      cudaSuccess)
     return 0;
   int per_sm = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBatchThreads, kBatchSmem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<ROWS>, kBatchThreads, kBatchSmem) !=
+      cudaSuccess)
     return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   cached[dev] = (per_sm < 1 ? 1 : per_sm) * sms;
   return cached[dev];
 }
+
+int batch_resident_blocks_rows(RowMode rows) {
+  return rows == kRowsFixed ? batch_resident_blocks_t<kRowsFixed>() : batch_resident_blocks_t<kRowsF64>();
+}
+
+int batch_resident_blocks() { return batch_resident_blocks_rows(rows_from_env()); }
 
 }  // namespace perm
 
@@ -150,7 +182,10 @@ std::mutex g_batch_mu;
 struct Tune {
   int L[kBatchNMax + 1] = {0};
 };
-Tune g_tune[64];
+Tune g_tune_tab[2][64];  // [row mode][device]
+
+// Tuning table of the row arithmetic currently selected (PERM_ROWS).
+Tune& tune_of(int dev) { return g_tune_tab[rows_from_env() == kRowsFixed ? 1 : 0][dev]; }
 
 int default_L(int n) {
   // about 16 n codes per lane keeps the O(n^2) seed near 2% of the walk
@@ -216,6 +251,7 @@ struct Plan {
   void* out = nullptr;
   std::vector<int> ns;
   std::vector<int> Ls;
+  RowMode rows = kRowsFixed;
   DevBuf items, partials, mfirst, mcount, mn, ticket;
   int nitems = 0;
   cudaGraphExec_t exec = nullptr;
@@ -229,12 +265,15 @@ constexpr size_t kMaxPlans = 8;
 
 int enqueue_batch(const double* const* ptrs, const BatchItem* d_items, int nitems, double* d_partials,
                   const int* d_mfirst, const int* d_mcount, const int* d_mn, int count, unsigned int* d_ticket,
-                  double* out, int* status, cudaStream_t s) {
-  const int grid = batch_resident_blocks();
+                  double* out, int* status, cudaStream_t s, RowMode rows) {
+  const int grid = batch_resident_blocks_rows(rows);
   if (grid < 1) return PERM_ECUDA;
   cudaError_t e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return status_of_b(e);
-  k_batch<<<grid, kBatchThreads, kBatchSmem, s>>>(ptrs, d_items, nitems, d_partials, d_ticket, status);
+  if (rows == kRowsFixed)
+    k_batch<kRowsFixed><<<grid, kBatchThreads, kBatchSmem, s>>>(ptrs, d_items, nitems, d_partials, d_ticket, status);
+  else
+    k_batch<kRowsF64><<<grid, kBatchThreads, kBatchSmem, s>>>(ptrs, d_items, nitems, d_partials, d_ticket, status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return status_of_b(e);
   if (out) {
@@ -268,7 +307,7 @@ int time_candidate(int n, int L, const double* const* d_ptrs, int m, double* ms_
   for (int rep = 0; rep < 3 && rc == PERM_OK; ++rep) {
     cudaEventRecord(e0, nullptr);
     rc = enqueue_batch(d_ptrs, (BatchItem*)di.p, (int)items.size(), (double*)dp.p, nullptr, nullptr, nullptr, 0,
-                       (unsigned int*)dt.p, nullptr, status, nullptr);
+                       (unsigned int*)dt.p, nullptr, status, nullptr, rows_from_env());
     cudaEventRecord(e1, nullptr);
     if (cudaEventSynchronize(e1) != cudaSuccess) rc = PERM_ECUDA;
     float ms = 0.f;
@@ -282,9 +321,9 @@ int time_candidate(int n, int L, const double* const* d_ptrs, int m, double* ms_
 }
 
 int autotune_order(int dev, int n) {
-  if (g_tune[dev].L[n]) return PERM_OK;
+  if (tune_of(dev).L[n]) return PERM_OK;
   if (!tuning_enabled() || n < 4) {
-    g_tune[dev].L[n] = default_L(n);
+    tune_of(dev).L[n] = default_L(n);
     return PERM_OK;
   }
   // synthetic matrix (fixed linear congruential values in [-1, 1)), replicated
@@ -313,7 +352,7 @@ int autotune_order(int dev, int n) {
     const double rate = (double)per * m / ms;
     if (rate > best_rate * 1.01) best_rate = rate, bestL = L;
   }
-  g_tune[dev].L[n] = bestL;
+  tune_of(dev).L[n] = bestL;
   return PERM_OK;
 }
 
@@ -331,7 +370,7 @@ int perm_batch_autotune(int n_lo, int n_hi) {
   if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return PERM_ECUDA;
   std::lock_guard<std::mutex> lk(g_batch_mu);
   for (int n = n_lo; n <= n_hi; ++n) {
-    g_tune[dev].L[n] = 0;
+    tune_of(dev).L[n] = 0;
     int rc = autotune_order(dev, n);
     if (rc) return rc;
   }
@@ -360,9 +399,9 @@ int perm_batch(const double* const* ptrs, const int* ns, int count, double* out,
   bool seen[kBatchNMax + 1] = {false};
   for (int k = 0; k < count; ++k) seen[ns[k]] = true;
   for (int n = 1; n <= kBatchNMax; ++n) {
-    if (!seen[n] || g_tune[dev].L[n]) continue;
+    if (!seen[n] || tune_of(dev).L[n]) continue;
     if (cap != cudaStreamCaptureStatusNone) {
-      g_tune[dev].L[n] = default_L(n);  // no timing while the caller captures
+      tune_of(dev).L[n] = default_L(n);  // no timing while the caller captures
     } else {
       int rc = autotune_order(dev, n);
       if (rc) return rc;
@@ -374,10 +413,11 @@ int perm_batch(const double* const* ptrs, const int* ns, int count, double* out,
   for (auto it = g_plans.begin(); it != g_plans.end(); ++it) {
     Plan* p = it->get();
     if (p->dev == dev && p->stream == s && p->ptrs == (const void*)ptrs && p->out == (void*)out &&
+        p->rows == rows_from_env() &&
         (int)p->ns.size() == count && std::memcmp(p->ns.data(), ns, count * sizeof(int)) == 0) {
       bool sameL = true;
       for (int n = 1; n <= kBatchNMax; ++n)
-        if (seen[n] && p->Ls[n] != g_tune[dev].L[n]) sameL = false;
+        if (seen[n] && p->Ls[n] != tune_of(dev).L[n]) sameL = false;
       if (!sameL) break;
       g_plans.splice(g_plans.begin(), g_plans, it);
       plan = p;
@@ -391,10 +431,11 @@ int perm_batch(const double* const* ptrs, const int* ns, int count, double* out,
     np->ptrs = ptrs;
     np->out = out;
     np->ns.assign(ns, ns + count);
-    np->Ls.assign(g_tune[dev].L, g_tune[dev].L + kBatchNMax + 1);
+    np->rows = rows_from_env();
+    np->Ls.assign(tune_of(dev).L, tune_of(dev).L + kBatchNMax + 1);
     std::vector<BatchItem> items;
     std::vector<int> mf, mc;
-    build_items(ns, count, g_tune[dev].L, items, mf, mc);
+    build_items(ns, count, tune_of(dev).L, items, mf, mc);
     np->nitems = (int)items.size();
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&np->items.p, items.size() * sizeof(BatchItem));
@@ -417,7 +458,8 @@ int perm_batch(const double* const* ptrs, const int* ns, int count, double* out,
     int rc = PERM_OK;
     if (e == cudaSuccess) {
       rc = enqueue_batch(ptrs, (BatchItem*)np->items.p, np->nitems, (double*)np->partials.p, (int*)np->mfirst.p,
-                         (int*)np->mcount.p, (int*)np->mn.p, count, (unsigned int*)np->ticket.p, out, status, cs);
+                         (int*)np->mcount.p, (int*)np->mn.p, count, (unsigned int*)np->ticket.p, out, status, cs,
+                         np->rows);
       cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
       if (rc == PERM_OK && e2 != cudaSuccess) rc = status_of_b(e2);
     } else {

@@ -1,0 +1,485 @@
+// Gray-code walk with exact fixed-point row sums (the same sum as
+// glynn_walk.cuh: Sec. 2.A, App. A).
+//
+// Each row i of A is scaled by its own power of two 2^F_i (chosen so that
+// sum_j |a_ij| 2^F_i < 2^62) and rounded once to int64: A_ij = rint(a_ij 2^F_i).
+// The row sums are then carried in Glynn's form v_i = 2 w_i = sum_{j<n} e_j
+// A_ij + A_{i,n} (e_j = +-1) as exact int64: the per-code update is an
+// integer add of +-2 A_ij, so the row sums never drift and need no re-seeding;
+// the only rounding in a row sum is the one-time rounding of A to 2^-F_i,
+// at least as fine as a 53-bit double of the row's largest sum.
+//
+// Per code, each v_i is turned into the double w_i = v_i 2^(-F_i - 1) with
+// integer bit operations (sign, count of leading zeros, shift, exponent
+// field; truncated to 53 bits), and the product and the signed accumulation
+// run in FP64 exactly as in the floating-point walk (or, in the FP32-product
+// mode, v_i is split straight into an FP32 significand and an integer
+// exponent).
+//
+// GB300 note: DFMA issues at 1/64 of the FP32 rate on this part while the
+// integer pipes run at half the FP32 rate, so moving the 2n row-update adds
+// per code to the integer pipes leaves the FP64 pipe with the 4(n-1) product
+// operations only (complex), a 1.5x reduction of its work at n = 40.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "dd.cuh"
+#include "glynn_walk.cuh"
+#include "perm_internal.h"
+
+namespace perm {
+
+template <int N, bool CPLX>
+struct FxShape {
+  static constexpr int E = CPLX ? 2 : 1;
+  // +2A and -2A tables (int64, column-major), v0 (int64), per-row exponent bias (int), dd reduction slots
+  static constexpr size_t table_bytes = (size_t)N * N * E * sizeof(long long);
+  static constexpr size_t smem_bytes = 2 * table_bytes + (size_t)N * E * sizeof(long long) + N * sizeof(int) +
+                                       8 * sizeof(dd) + 16;
+};
+
+// Double with value v * 2^(eb - 1086) (eb = 1086 - scale exponent), from the
+// bits of v only: |v| normalised by its leading-zero count, 52 fraction bits
+// kept (truncation).  0 for v == 0 and for results below the normal range.
+__device__ __forceinline__ double fx_to_double(long long v, int eb) {
+  const unsigned long long s = (unsigned long long)(v >> 63);
+  const unsigned long long m = ((unsigned long long)v ^ s) - s;
+  const int lz = __clzll((long long)m);
+  const unsigned long long mn = m << (lz & 63);
+  const uint32_t hi = (uint32_t)(mn >> 32), lo = (uint32_t)mn;
+  const int be = eb - lz;  // biased exponent of the result
+  const uint32_t dhi = ((uint32_t)s & 0x80000000u) | ((uint32_t)be << 20) | ((hi >> 11) & 0xFFFFFu);
+  const uint32_t dlo = (hi << 21) | (lo >> 11);
+  return (m == 0 || be <= 0) ? 0.0 : __hiloint2double((int)dhi, (int)dlo);
+}
+
+// FP32 significand of v scaled by 2^-(63 - lzref), i.e. relative to a number
+// whose leading one sits at bit 63 - lzref; 0 when v == 0 or far below.
+__device__ __forceinline__ float fx_to_f32(long long v, int lzref) {
+  const unsigned long long s = (unsigned long long)(v >> 63);
+  const unsigned long long m = ((unsigned long long)v ^ s) - s;
+  const int lz = __clzll((long long)m);
+  const unsigned long long mn = m << (lz & 63);
+  const int fexp = 127 + lzref - lz;
+  const uint32_t bits = ((uint32_t)s & 0x80000000u) | ((uint32_t)fexp << 23) | ((uint32_t)(mn >> 40) & 0x7FFFFFu);
+  return (m == 0 || fexp <= 0) ? 0.0f : __int_as_float((int)bits);
+}
+
+template <int N, bool CPLX, int MODE>
+struct FxProduct;
+
+// FP64 product of w_i = v_i 2^(eb_i - 1086), two interleaved chains.
+template <int N>
+struct FxProduct<N, true, kProdF64> {
+  static __device__ __forceinline__ void eval(const long long (&vr)[N], const long long (&vi)[N], const int* sEb,
+                                              double& pr, double& pi, double z) {
+    double ar = fx_to_double(vr[0], sEb[0]), ai = fx_to_double(vi[0], sEb[0]);
+    if constexpr (N == 1) {
+      pr = ar;
+      pi = ai;
+    } else {
+      double br = fx_to_double(vr[1], sEb[1]), bi = fx_to_double(vi[1], sEb[1]);
+#pragma unroll
+      for (int i = 2; i < N; ++i) {
+        const int eb = sEb[i];
+        const double cr = fx_to_double(vr[i], eb), ci = fx_to_double(vi[i], eb);
+        if (i & 1)
+          cmul(br, bi, cr, ci, z);
+        else
+          cmul(ar, ai, cr, ci, z);
+      }
+      cmul(ar, ai, br, bi, z);
+      pr = ar;
+      pi = ai;
+    }
+  }
+};
+
+template <int N>
+struct FxProduct<N, false, kProdF64> {
+  static __device__ __forceinline__ void eval(const long long (&v)[N], const int* sEb, double& p, double z) {
+    double a = fx_to_double(v[0], sEb[0]);
+    if constexpr (N == 1) {
+      p = a;
+    } else {
+      double b = fx_to_double(v[1], sEb[1]);
+#pragma unroll
+      for (int i = 2; i < N; ++i) {
+        const double c = fx_to_double(v[i], sEb[i]);
+        if (i & 1)
+          b = fma(b, c, z);
+        else
+          a = fma(a, c, z);
+      }
+      p = fma(a, b, z);
+    }
+  }
+};
+
+// FP32 significands straight from the integers; exponents add in integers.
+template <int N>
+struct FxProduct<N, true, kProdF32> {
+  static __device__ __forceinline__ void eval(const long long (&vr)[N], const long long (&vi)[N], const int* sEb,
+                                              double& pr, double& pi, double) {
+    float ar = 1.f, ai = 0.f, br = 1.f, bi = 0.f;
+    int E = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const unsigned long long sr = (unsigned long long)(vr[i] >> 63), si = (unsigned long long)(vi[i] >> 63);
+      const int lzr = __clzll((long long)((vr[i] ^ sr) - sr));
+      const int lzi = __clzll((long long)((vi[i] ^ si) - si));
+      const int lzref = min(lzr, lzi);
+      const float fr = fx_to_f32(vr[i], lzref);
+      const float fi = fx_to_f32(vi[i], lzref);
+      // |w_i| = |f| 2^(63 - lzref + eb_i - 1086)
+      E += 63 - lzref + sEb[i] - 1086;
+      if (i == 0) {
+        ar = fr, ai = fi;
+      } else if (i == 1) {
+        br = fr, bi = fi;
+      } else if (i & 1) {
+        cmulf(br, bi, fr, fi);
+      } else {
+        cmulf(ar, ai, fr, fi);
+      }
+    }
+    if constexpr (N > 1) cmulf(ar, ai, br, bi);
+    pr = f32_times_pow2(ar, E);
+    pi = f32_times_pow2(ai, E);
+  }
+};
+
+template <int N>
+struct FxProduct<N, false, kProdF32> {
+  static __device__ __forceinline__ void eval(const long long (&v)[N], const int* sEb, double& p, double) {
+    float a = 1.f, b = 1.f;
+    int E = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const unsigned long long s = (unsigned long long)(v[i] >> 63);
+      const int lz = __clzll((long long)((v[i] ^ s) - s));
+      const float f = fx_to_f32(v[i], lz);
+      E += 63 - lz + sEb[i] - 1086;
+      if (i & 1)
+        b *= f;
+      else
+        a *= f;
+    }
+    p = f32_times_pow2(a * b, E);
+  }
+};
+
+// Stage: per-row scale exponents, the +-2A tables and v0, from global memory.
+// Returns (block-uniform) whether any entry is non-finite.
+template <int N, bool CPLX>
+__device__ __forceinline__ bool fx_stage(const double* __restrict__ A, long long* sP, long long* sM, long long* sV0,
+                                         int* sEb, int* sF, int* status) {
+  constexpr int E = CPLX ? 2 : 1;
+  int bad = 0;
+  if (threadIdx.x < N) {
+    const int i = threadIdx.x;
+    double mx = 0.0;
+#pragma unroll
+    for (int c = 0; c < E; ++c) {
+      double s = 0.0;
+      for (int j = 0; j < N; ++j) {
+        const double v = A[((size_t)i * N + j) * E + c];
+        bad |= not_finite(v) ? 1 : 0;
+        s += fabs(v);
+      }
+      mx = fmax(mx, s);
+    }
+    // 2^F_i with sum_j |a_ij| 2^F_i < 2^62: F_i = 61 - floor(log2 max_c sum_j |a_ij|)
+    int F = 0;
+    if (mx > 0.0 && !bad) {
+      const int ex = dexp_of(mx);
+      F = ex == 0 ? 61 + 1022 : 61 - (ex - 1023);  // subnormal sums: scale as the smallest normal
+    }
+    sF[i] = F;
+    sEb[i] = 1086 - F - 1;  // the extra -1 halves v = 2w into w
+  }
+  if (__syncthreads_or(bad)) {
+    if (threadIdx.x == 0) atomicOr(status, (int)kStatusNonFinite);
+    return true;
+  }
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    const int i = idx / N, j = idx - i * N;
+    const int F = sF[i];
+#pragma unroll
+    for (int c = 0; c < E; ++c) {
+      const long long q = __double2ll_rn(scalbn(A[(size_t)idx * E + c], F));
+      sP[(j * N + i) * E + c] = 2 * q;
+      sM[(j * N + i) * E + c] = -2 * q;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    const int i = threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < E; ++c) {
+      // v0_i = A_{i,n} - sum_{j<n} A_ij  (all e_j = -1), from the doubled table
+      long long s = sP[((N - 1) * N + i) * E + c];
+      for (int j = 0; j < N - 1; ++j) s -= sP[(j * N + i) * E + c];
+      sV0[i * E + c] = s / 2;
+    }
+  }
+  __syncthreads();
+  return false;
+}
+
+// TWO_TABLES: read -2A from its own table; otherwise negate +2A on the fly
+// (integer ops only; used where shared memory is tight).
+template <int N, int MODE, bool TWO_TABLES = true>
+__device__ __forceinline__ void thread_walk_c128_fx(const longlong2* __restrict__ sP, const longlong2* __restrict__ sM,
+                                                    const longlong2* __restrict__ sV0, const int* __restrict__ sEb,
+                                                    uint64_t r, const uint64_t end, dd& accr, dd& acci) {
+  if (r >= end) return;
+  const double z = fx_to_double(sV0[0].x, sEb[0]) * 0.0;  // a register zero (+-0.0) for the product FMAs
+  long long vr[N], vi[N];
+  {
+    // seed once (App. A steps 2, 5-8, in v = 2w form): exact, never redone
+    const uint64_t x = r ^ (r >> 1);
+    longlong2 seed[N];
+#pragma unroll 1
+    for (int i = 0; i < N; ++i) {
+      longlong2 v = sV0[i];
+#pragma unroll 1
+      for (int j = 0; j < N - 1; ++j) {
+        if ((x >> j) & 1ull) {
+          const longlong2 c = sP[j * N + i];
+          v.x += c.x;
+          v.y += c.y;
+        }
+      }
+      seed[i] = v;
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      vr[i] = seed[i].x;
+      vi[i] = seed[i].y;
+    }
+  }
+  while (r < end) {
+    const uint64_t run_end = min(end, (r | (kRun - 1)) + 1);
+    double sr = 0.0, si = 0.0;
+    uint32_t odd = (uint32_t)(r & 1ull);
+    for (; r < run_end; ++r) {
+      double pr, pi;
+      FxProduct<N, true, MODE>::eval(vr, vi, sEb, pr, pi, z);
+      const double sg = pm_one(odd);
+      odd ^= 1u;
+      sr = fma(sg, pr, sr);
+      si = fma(sg, pi, si);
+      int j;
+      uint32_t neg;
+      gray_step(r, j, neg);
+      if constexpr (TWO_TABLES) {
+        const longlong2* col = (neg ? sM : sP) + j * N;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const longlong2 c = col[i];
+          vr[i] += c.x;
+          vi[i] += c.y;
+        }
+      } else {
+        const longlong2* col = sP + j * N;
+        const long long m = -(long long)neg;  // 0 or all ones
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const longlong2 c = col[i];
+          vr[i] += (c.x ^ m) - m;
+          vi[i] += (c.y ^ m) - m;
+        }
+      }
+    }
+    accr = dd_add_d(accr, sr);
+    acci = dd_add_d(acci, si);
+  }
+}
+
+// Warp-level staging of one complex matrix of order n (<= 32) into a warp's
+// own slot: row scales, the +2A table (column-major) and v0.  Returns whether
+// any entry is non-finite (warp-uniform).
+__device__ __forceinline__ bool fx_stage_warp_c128(const double2* __restrict__ A, int n, longlong2* sP, longlong2* sV0,
+                                                   int* sEb, int* sF) {
+  const int lane = threadIdx.x & 31;
+  int bad = 0;
+  if (lane < n) {
+    double sr = 0.0, si = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const double2 v = A[lane * n + j];
+      bad |= (not_finite(v.x) || not_finite(v.y)) ? 1 : 0;
+      sr += fabs(v.x);
+      si += fabs(v.y);
+    }
+    const double mx = fmax(sr, si);
+    int F = 0;
+    if (mx > 0.0 && !bad) {
+      const int ex = dexp_of(mx);
+      F = ex == 0 ? 61 + 1022 : 61 - (ex - 1023);
+    }
+    sF[lane] = F;
+    sEb[lane] = 1086 - F - 1;
+  }
+  if (__any_sync(0xffffffffu, bad)) return true;
+  __syncwarp();
+  for (int idx = lane; idx < n * n; idx += 32) {
+    const int i = idx / n, j = idx - i * n;
+    const int F = sF[i];
+    const double2 v = A[idx];
+    sP[j * n + i] = make_longlong2(2 * __double2ll_rn(scalbn(v.x, F)), 2 * __double2ll_rn(scalbn(v.y, F)));
+  }
+  __syncwarp();
+  if (lane < n) {
+    longlong2 s = sP[(n - 1) * n + lane];
+    for (int j = 0; j < n - 1; ++j) {
+      s.x -= sP[j * n + lane].x;
+      s.y -= sP[j * n + lane].y;
+    }
+    sV0[lane] = make_longlong2(s.x / 2, s.y / 2);
+  }
+  __syncwarp();
+  return false;
+}
+
+template <int N, int MODE>
+__device__ __forceinline__ void thread_walk_r64_fx(const long long* __restrict__ sP, const long long* __restrict__ sM,
+                                                   const long long* __restrict__ sV0, const int* __restrict__ sEb,
+                                                   uint64_t r, const uint64_t end, dd& accr) {
+  if (r >= end) return;
+  const double z = fx_to_double(sV0[0], sEb[0]) * 0.0;
+  long long v[N];
+  {
+    const uint64_t x = r ^ (r >> 1);
+    long long seed[N];
+#pragma unroll 1
+    for (int i = 0; i < N; ++i) {
+      long long s = sV0[i];
+#pragma unroll 1
+      for (int j = 0; j < N - 1; ++j)
+        if ((x >> j) & 1ull) s += sP[j * N + i];
+      seed[i] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = seed[i];
+  }
+  while (r < end) {
+    const uint64_t run_end = min(end, (r | (kRun - 1)) + 1);
+    double s = 0.0;
+    uint32_t odd = (uint32_t)(r & 1ull);
+    for (; r < run_end; ++r) {
+      double p;
+      FxProduct<N, false, MODE>::eval(v, sEb, p, z);
+      s = fma(pm_one(odd), p, s);
+      odd ^= 1u;
+      int j;
+      uint32_t neg;
+      gray_step(r, j, neg);
+      const long long* col = (neg ? sM : sP) + j * N;
+#pragma unroll
+      for (int i = 0; i < N; ++i) v[i] += col[i];
+    }
+    accr = dd_add_d(accr, s);
+  }
+}
+
+template <int N, bool CPLX, int MODE>
+__global__ void __launch_bounds__(kWalkThreads) k_walk_fx(const double* __restrict__ A, uint64_t first, uint64_t count,
+                                                          double* __restrict__ partials, int accumulate,
+                                                          int* __restrict__ status) {
+  constexpr int E = CPLX ? 2 : 1;
+  extern __shared__ __align__(16) long long fsm[];
+  long long* sP = fsm;
+  long long* sM = sP + N * N * E;
+  long long* sV0 = sM + N * N * E;
+  int* sEb = reinterpret_cast<int*>(sV0 + N * E);
+  int* sF = sEb + N;
+  dd* sRed = reinterpret_cast<dd*>(fsm) ;  // reused after the walk (tables no longer read)
+
+  const bool bad = fx_stage<N, CPLX>(A, sP, sM, sV0, sEb, sF, status);
+
+  uint64_t r, end;
+  thread_range(first, count, r, end);
+  dd accr{0.0, 0.0}, acci{0.0, 0.0};
+  if (!bad) {
+    if constexpr (CPLX)
+      thread_walk_c128_fx<N, MODE>(reinterpret_cast<const longlong2*>(sP), reinterpret_cast<const longlong2*>(sM),
+                                   reinterpret_cast<const longlong2*>(sV0), sEb, r, end, accr, acci);
+    else
+      thread_walk_r64_fx<N, MODE>(sP, sM, sV0, sEb, r, end, accr);
+  } else {
+    accr = dd{__longlong_as_double(0x7ff8000000000000ll), 0.0};
+    acci = accr;
+  }
+  __syncthreads();  // every thread is done with the tables before they are reused
+  block_store<CPLX>(accr, acci, sRed, partials, accumulate);
+}
+
+template <int N, bool CPLX, int MODE>
+struct FxKernel {
+  static constexpr size_t smem = FxShape<N, CPLX>::smem_bytes;
+
+  static cudaError_t prepare(int& resident) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static int cached[64] = {0};
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (cached[dev] > 0) {
+      resident = cached[dev];
+      return cudaSuccess;
+    }
+    if (smem > 48 * 1024) {
+      e = cudaFuncSetAttribute(k_walk_fx<N, CPLX, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_fx<N, CPLX, MODE>, kWalkThreads, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    cached[dev] = per_sm * sms;
+    resident = cached[dev];
+    return cudaSuccess;
+  }
+
+  static int resident_blocks() {
+    int r = 0;
+    return prepare(r) == cudaSuccess ? r : 0;
+  }
+
+  static cudaError_t launch(const WalkArgs& a) {
+    int resident = 0;
+    cudaError_t e = prepare(resident);
+    if (e != cudaSuccess) return e;
+    k_walk_fx<N, CPLX, MODE><<<a.blocks, kWalkThreads, smem, a.stream>>>(a.A, a.first, a.count, a.partials,
+                                                                         a.accumulate, a.status);
+    return cudaGetLastError();
+  }
+};
+
+template <bool CPLX, int MODE, int LO, int HI>
+cudaError_t fx_dispatch(const WalkArgs& a) {
+  if constexpr (LO > HI) {
+    return cudaErrorInvalidValue;
+  } else {
+    if (a.n == LO) return FxKernel<LO, CPLX, MODE>::launch(a);
+    return fx_dispatch<CPLX, MODE, LO + 1, HI>(a);
+  }
+}
+
+template <bool CPLX, int MODE, int LO, int HI>
+int fx_blocks_dispatch(int n) {
+  if constexpr (LO > HI) {
+    return 0;
+  } else {
+    if (n == LO) return FxKernel<LO, CPLX, MODE>::resident_blocks();
+    return fx_blocks_dispatch<CPLX, MODE, LO + 1, HI>(n);
+  }
+}
+
+}  // namespace perm

@@ -94,7 +94,8 @@ extern "C" int perm_c128_noalloc(const double* A, int n, double* out, void* stre
   int* status = reinterpret_cast<int*>(scratch + (size_t)kNoAllocMaxBlocks * 4);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-  const int resident = walk_resident_blocks(n, true, kProdF64);
+  const RowMode rows = rows_from_env();  // the same kernel perm_c128 uses
+  const int resident = walk_resident_blocks(n, true, kProdF64, rows);
   if (resident < 1) {
     cudaGetLastError();
     return PERM_ECUDA;
@@ -113,7 +114,7 @@ extern "C" int perm_c128_noalloc(const double* A, int n, double* out, void* stre
   do {
     const uint64_t len = (count - done) < kNoAllocCodesPerLaunch ? (count - done) : kNoAllocCodesPerLaunch;
     WalkArgs a{A, n, done, len, partials, blocks, done > 0 ? 1 : 0, status, s};
-    e = walk_launch(true, kProdF64, a);
+    e = walk_launch(true, kProdF64, a, rows);
     if (e != cudaSuccess) return PERM_ECUDA;
     done += len;
   } while (done < count);

@@ -89,7 +89,19 @@ int device_status_word(int dev, int** out) {
   return 0;
 }
 
-int walk_resident_blocks(int n, bool cplx, ProductMode mode) {
+RowMode rows_from_env() {
+  const char* e = std::getenv("PERM_ROWS");
+  return (e && std::strcmp(e, "fp64") == 0) ? kRowsF64 : kRowsFixed;
+}
+
+int walk_resident_blocks(int n, bool cplx, ProductMode mode, RowMode rows) {
+  if (rows == kRowsFixed) {
+    if (mode == kProdF64) {
+      if (cplx) return n <= 32 ? walk_blocks_fx_c128_f64_lo(n) : walk_blocks_fx_c128_f64_hi(n);
+      return walk_blocks_fx_r64_f64(n);
+    }
+    return cplx ? walk_blocks_fx_c128_f32(n) : walk_blocks_fx_r64_f32(n);
+  }
   if (mode == kProdF64) {
     if (cplx) return n <= 32 ? walk_blocks_c128_f64_lo(n) : walk_blocks_c128_f64_hi(n);
     return walk_blocks_r64_f64(n);
@@ -97,7 +109,14 @@ int walk_resident_blocks(int n, bool cplx, ProductMode mode) {
   return cplx ? walk_blocks_c128_f32(n) : walk_blocks_r64_f32(n);
 }
 
-cudaError_t walk_launch(bool cplx, ProductMode mode, const WalkArgs& a) {
+cudaError_t walk_launch(bool cplx, ProductMode mode, const WalkArgs& a, RowMode rows) {
+  if (rows == kRowsFixed) {
+    if (mode == kProdF64) {
+      if (cplx) return a.n <= 32 ? walk_launch_fx_c128_f64_lo(a) : walk_launch_fx_c128_f64_hi(a);
+      return walk_launch_fx_r64_f64(a);
+    }
+    return cplx ? walk_launch_fx_c128_f32(a) : walk_launch_fx_r64_f32(a);
+  }
   if (mode == kProdF64) {
     if (cplx) return a.n <= 32 ? walk_launch_c128_f64_lo(a) : walk_launch_c128_f64_hi(a);
     return walk_launch_r64_f64(a);
@@ -188,7 +207,8 @@ int run_walk(bool cplx, ProductMode pm, const double* A, int n, uint64_t first, 
   const bool a_dev = is_device_ptr(A);
   const bool o_dev = is_device_ptr(out);
 
-  int resident = walk_resident_blocks(n, cplx, pm);
+  const RowMode rows = rows_from_env();
+  int resident = walk_resident_blocks(n, cplx, pm, rows);
   if (resident < 1) {
     cudaGetLastError();
     return PERM_ECUDA;
@@ -216,7 +236,7 @@ int run_walk(bool cplx, ProductMode pm, const double* A, int n, uint64_t first, 
   do {
     const uint64_t len = (count - done) < kCodesPerLaunch ? (count - done) : kCodesPerLaunch;
     WalkArgs a{dA, n, first + done, len, partials, blocks, done > 0 ? 1 : 0, status, s};
-    cudaError_t e = walk_launch(cplx, pm, a);
+    cudaError_t e = walk_launch(cplx, pm, a, rows);
     if (e != cudaSuccess) return status_of(e);
     done += len;
   } while (done < count);

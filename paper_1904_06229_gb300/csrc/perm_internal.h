@@ -19,6 +19,16 @@ enum ProductMode : int {
   kProdF32 = 1,  // FP32 significands with integer exponents
 };
 
+// Row-sum arithmetic of a walk kernel.
+enum RowMode : int {
+  kRowsF64 = 0,    // FP64 row sums, DFMA updates, periodic re-seed (glynn_walk.cuh)
+  kRowsFixed = 1,  // exact int64 fixed-point row sums, integer updates (glynn_walk_fx.cuh)
+};
+
+// Row arithmetic for the floating-point entry points: PERM_ROWS=fp64 selects
+// kRowsF64, anything else (default) kRowsFixed.
+RowMode rows_from_env();
+
 struct WalkArgs {
   const double* A;     // device, row-major (interleaved re/im when complex)
   int n;               // order
@@ -32,10 +42,10 @@ struct WalkArgs {
 };
 
 // Largest useful grid for one walk launch (resident blocks on the device).
-int walk_resident_blocks(int n, bool cplx, ProductMode mode);
+int walk_resident_blocks(int n, bool cplx, ProductMode mode, RowMode rows = kRowsF64);
 
-// Launch the Gray-walk kernel for the given order / type / product mode.
-cudaError_t walk_launch(bool cplx, ProductMode mode, const WalkArgs& a);
+// Launch the Gray-walk kernel for the given order / type / product / row mode.
+cudaError_t walk_launch(bool cplx, ProductMode mode, const WalkArgs& a, RowMode rows = kRowsF64);
 
 // Per-order dispatch inside each kernel translation unit.
 cudaError_t walk_launch_c128_f64_lo(const WalkArgs& a);   // n in 1..32
@@ -43,6 +53,16 @@ cudaError_t walk_launch_c128_f64_hi(const WalkArgs& a);   // n in 33..64
 cudaError_t walk_launch_r64_f64(const WalkArgs& a);       // n in 1..64
 cudaError_t walk_launch_c128_f32(const WalkArgs& a);      // n in 1..64
 cudaError_t walk_launch_r64_f32(const WalkArgs& a);       // n in 1..64
+cudaError_t walk_launch_fx_c128_f64_lo(const WalkArgs& a);  // fixed-point rows
+cudaError_t walk_launch_fx_c128_f64_hi(const WalkArgs& a);
+cudaError_t walk_launch_fx_r64_f64(const WalkArgs& a);
+cudaError_t walk_launch_fx_c128_f32(const WalkArgs& a);
+cudaError_t walk_launch_fx_r64_f32(const WalkArgs& a);
+int walk_blocks_fx_c128_f64_lo(int n);
+int walk_blocks_fx_c128_f64_hi(int n);
+int walk_blocks_fx_r64_f64(int n);
+int walk_blocks_fx_c128_f32(int n);
+int walk_blocks_fx_r64_f32(int n);
 int walk_blocks_c128_f64_lo(int n);
 int walk_blocks_c128_f64_hi(int n);
 int walk_blocks_r64_f64(int n);

@@ -1,0 +1,10 @@
+// Instantiations of the fixed-point-row Gray walk: complex matrices, FP64 products, orders 33..64.
+#include "glynn_walk_fx.cuh"
+
+namespace perm {
+
+cudaError_t walk_launch_fx_c128_f64_hi(const WalkArgs& a) { return fx_dispatch<true, kProdF64, 33, 64>(a); }
+
+int walk_blocks_fx_c128_f64_hi(int n) { return fx_blocks_dispatch<true, kProdF64, 33, 64>(n); }
+
+}  // namespace perm

@@ -14,6 +14,12 @@ pytestmark = pytest.mark.gpu
 U32 = 2.0 ** -24
 
 
+@pytest.fixture(autouse=True, params=["fixed", "fp64"])
+def rows(request, monkeypatch):
+    monkeypatch.setenv("PERM_ROWS", request.param)
+    return request.param
+
+
 def _bound(n, asum):
     return (2 * n + 2) * U32 * asum
 
