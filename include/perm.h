@@ -111,6 +111,34 @@ int perm_c128_noalloc(const double* A, int n, double* out, void* stream);
 int perm_c128_f32p(const double* A, int n, double* out, void* stream);
 int perm_f64_f32p(const double* A, int n, double* out, void* stream);
 
+/* ---- Repeated columns: the weighted Ryser formula, Eq.(ryser2) of Sec. 2.A ----
+ *   per(A) = (-1)^n sum_{0<=f_k<=m_k} (-1)^{sum f} (prod_k binom(m_k, f_k)) prod_i sum_k f_k cbar_k(i)
+ * for the n x n matrix A whose R distinct columns cbar_1..cbar_R appear m_k
+ * times each (sum_k m_k = n; Boson-sampling outputs with several photons in
+ * one mode give such matrices).  prod_k (m_k + 1) terms instead of 2^(n-1).
+ * C: n x R complex matrix of the distinct columns, row-major interleaved
+ *    (C[2*(i*R+k)] = Re cbar_k(i)); device or host memory.
+ * mult: HOST array of R multiplicities >= 1 summing to n; 1 <= R <= n <= 64;
+ *    at most 2^62 terms (PERM_EINVAL otherwise).
+ * out: 2 doubles (re, im), device or host.  Row sums are exact int64 fixed
+ * point, products FP64, accumulation double-double; rows of A are not
+ * merged (use the transpose for repeated rows: per(A) = per(A^T)). */
+int perm_c128_repeated(const double* C, const int* mult, int R, int n, double* out, void* stream);
+
+/* ---- Band matrices: the transfer-matrix recursion of App. C ("bandpermanent") ----
+ * For A with a_ij = 0 whenever |i - j| > k: multiply the linear forms
+ * C_i = sum_j a_ij x_j row by row with x_j^2 = 0, setting x_{i-k-1} = 1 once
+ * no later row involves it, then all x = 1.  O(n 2^(2k+1) (2k+1)) work,
+ * linear in n for fixed k.
+ * A: `count` complex n x n matrices, contiguous (count * 2*n*n doubles,
+ *    row-major interleaved), device or host; only entries with |i - j| <= k
+ *    are read (the others are taken as zero).
+ * n: 1..65535; k: 0..5; count >= 1.  out: 2*count doubles (re, im), device
+ * or host.  One CTA per matrix; the window polynomial (2^(2k+1) complex
+ * coefficients) lives in shared memory; coefficients are formed in a fixed
+ * order (deterministic). */
+int perm_c128_band(const double* A, int n, int k, int count, double* out, void* stream);
+
 /* ---- Batch of independent complex permanents (the random-matrix studies of
  * Secs. 3-6 need 10^5..10^7 permanents of orders up to ~35) ----
  * ptrs: DEVICE array of `count` DEVICE pointers, each to a 2*n_k*n_k complex

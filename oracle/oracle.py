@@ -73,6 +73,7 @@ def _load():
             lib.oracle_glynn_mod_range_i8.argtypes = [ld_p, ctypes.c_int, ld_p, ctypes.c_int, u64, u64, ld_p]
             lib.oracle_per_mod_i8.argtypes = [ld_p, ctypes.c_int, ld_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ld_p]
+            lib.oracle_ryser2_c.argtypes = [ld_p, ctypes.c_int, ctypes.c_int, ld_p, ld_p]
             _lib = lib
     return _lib
 
@@ -191,6 +192,27 @@ def _compensated(xs):
     return s + c
 
 
+def per_repeated(Cbar, mult):
+    """Eq.(ryser2): permanent of the n x n matrix whose distinct columns are the
+    R columns of `Cbar` (n x R), column k repeated mult[k] times.  Long double,
+    plain counting order over the multiplicity vectors.  Returns (re, im)."""
+    c = np.ascontiguousarray(np.asarray(Cbar).astype(np.complex128)).view(np.float64)
+    Cb = np.asarray(Cbar)
+    n, R = Cb.shape
+    m = np.ascontiguousarray(np.asarray(mult, dtype=np.int32))
+    out = np.zeros(2, dtype=np.longdouble)
+    rc = _load().oracle_ryser2_c(_ptr(c), int(n), int(R), _ptr(m), _ptr(out))
+    if rc != 0:
+        raise ValueError("bad repeated-column specification")
+    return out[0], out[1]
+
+
+def expand_columns(Cbar, mult):
+    """The n x n matrix with column k of Cbar repeated mult[k] times."""
+    Cb = np.asarray(Cbar)
+    return np.concatenate([np.repeat(Cb[:, k:k + 1], int(mk), axis=1) for k, mk in enumerate(mult)], axis=1)
+
+
 # ------------------------------------------------------------------- integers
 def _limbs_to_int(limbs) -> int:
     v = 0
@@ -297,6 +319,63 @@ def glynn_term_exact(A, r: int):
         pr, pi = pr * wr - pi * wi, pr * wi + pi * wr
     s = -1 if r & 1 else 1
     return s * pr, s * pi
+
+
+def band_permanent_exact(A, k: int):
+    """App. C "bandpermanent(A, k, p)" in exact rational arithmetic.
+
+    The polynomial p in the formal variables x_1..x_n is a dict from the
+    bitmask of a multilinear monomial to its coefficient (a pair of
+    Fractions).  For each row i: p := p * C_i with C_i = sum_j a_ij x_j
+    (only the entries inside the band |i - j| <= k; x_j^2 = 0 drops products
+    that repeat a variable), then x_{i-k-1} := 1 (its bit is cleared, merging
+    monomials); finally every x := 1 (the coefficients are summed).  The
+    entries outside the band must be zero (checked)."""
+    A = np.asarray(A)
+    n = A.shape[0]
+    for i in range(n):
+        for j in range(n):
+            if abs(i - j) > k and A[i, j] != 0:
+                raise ValueError("entry outside the band")
+    M = [[(_frac(np.real(A[i, j])), _frac(np.imag(A[i, j]))) for j in range(n)] for i in range(n)]
+    p = {0: (Fraction(1), Fraction(0))}
+    for i in range(n):  # 0-based row i is the paper's row i+1
+        q = {}
+        for S, (cr, ci) in p.items():
+            for j in range(max(0, i - k), min(n, i + k + 1)):
+                if (S >> j) & 1:
+                    continue  # x_j^2 = 0
+                ar, ai = M[i][j]
+                if ar == 0 and ai == 0:
+                    continue
+                T = S | (1 << j)
+                tr, ti = q.get(T, (Fraction(0), Fraction(0)))
+                q[T] = (tr + cr * ar - ci * ai, ti + cr * ai + ci * ar)
+        r = i - k - 1  # 0-based index of x_{i-k-1} for the paper's row i+1
+        if r >= 0:
+            merged = {}
+            for S, (cr, ci) in q.items():
+                S2 = S & ~(1 << r)
+                tr, ti = merged.get(S2, (Fraction(0), Fraction(0)))
+                merged[S2] = (tr + cr, ti + ci)
+            q = merged
+        p = q
+    sr = sum((c[0] for c in p.values()), Fraction(0))
+    si = sum((c[1] for c in p.values()), Fraction(0))
+    return sr, si
+
+
+def band_matrix(n: int, k: int, seed: int, kind: str = "gaussian"):
+    """Random complex band matrix (zero outside |i - j| <= k); the App. C
+    timing study uses real Gaussian entries (kind='real')."""
+    rng = np.random.default_rng(seed)
+    if kind == "real":
+        A = rng.standard_normal((n, n)).astype(np.complex128)
+    else:
+        A = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) * np.sqrt(0.5)
+    i, j = np.indices((n, n))
+    A[np.abs(i - j) > k] = 0
+    return A
 
 
 # ------------------------------------------------------- primes and the CRT

@@ -24,6 +24,9 @@
  *                        integers), for integer matrices.
  *   oracle_glynn_mod_i8  the same sum modulo 64-bit primes, products reduced
  *                        with unsigned __int128 division.
+ *   oracle_ryser2_c      Eq.(ryser2): the weighted Ryser sum for a matrix with
+ *                        repeated columns, over all multiplicity vectors f,
+ *                        row sums formed from scratch for every f.
  *
  * Real matrices are complex matrices with zero imaginary part; every function
  * takes an interleaved (re, im) row-major n x n array of doubles.
@@ -468,6 +471,59 @@ int oracle_per_mod_i8(const int8_t* A, int n, const uint64_t* primes, int k, int
   }
   free(part);
   return err ? -1 : 0;
+}
+
+/* ---- Eq.(ryser2): A has R distinct columns cbar_1..cbar_R, column k
+ * repeated m_k times (sum m_k = n).  C holds the distinct columns as an
+ * n x R row-major complex array (C[i][k] = cbar_k(i)).
+ *   per(A) = (-1)^n sum_{0 <= f_k <= m_k} (-1)^{sum f} (prod_k binom(m_k, f_k))
+ *            prod_i sum_k f_k cbar_k(i)
+ * The vectors f are visited in plain counting order (f_1 fastest); every
+ * row sum is formed from scratch. */
+static ld binom_ld(int m, int f) {
+  ld b = 1;
+  for (int t = 1; t <= f; ++t) b = b * (m - f + t) / t;
+  return b;
+}
+
+int oracle_ryser2_c(const double* C, int n, int R, const int* mult, ld* out) {
+  if (n < 1 || n > ORACLE_NMAX || R < 1 || R > n || !C || !mult || !out) return -1;
+  int tot = 0;
+  for (int k = 0; k < R; ++k) {
+    if (mult[k] < 1) return -1;
+    tot += mult[k];
+  }
+  if (tot != n) return -1;
+  int f[ORACLE_NMAX];
+  for (int k = 0; k < R; ++k) f[k] = 0;
+  csum sr = {0, 0}, si = {0, 0};
+  for (;;) {
+    ld wgt = 1;
+    int fs = 0;
+    for (int k = 0; k < R; ++k) wgt *= binom_ld(mult[k], f[k]), fs += f[k];
+    ld pr = 1, pi = 0;
+    for (int i = 0; i < n; ++i) {
+      ld rr = 0, ri = 0;
+      for (int k = 0; k < R; ++k) {
+        rr += f[k] * (ld)C[2 * ((size_t)i * R + k)];
+        ri += f[k] * (ld)C[2 * ((size_t)i * R + k) + 1];
+      }
+      ld nr = pr * rr - pi * ri, ni = pr * ri + pi * rr;
+      pr = nr, pi = ni;
+    }
+    ld sg = (fs & 1) ? -wgt : wgt;
+    csum_add(&sr, sg * pr);
+    csum_add(&si, sg * pi);
+    /* next f in counting order */
+    int k = 0;
+    while (k < R && f[k] == mult[k]) f[k] = 0, ++k;
+    if (k == R) break;
+    ++f[k];
+  }
+  ld s = (n & 1) ? -1 : 1;
+  out[0] = s * csum_value(&sr);
+  out[1] = s * csum_value(&si);
+  return 0;
 }
 
 int oracle_long_double_digits(void) { return LDBL_MANT_DIG; }

@@ -35,6 +35,8 @@ SOURCES = [
     "walk_fx_c128_f32.cu",
     "walk_fx_r64_f32.cu",
     "glynn_mod.cu",
+    "ryser2.cu",
+    "band.cu",
     "batch.cu",
     "perm_abi.cu",
     "peak.cu",

@@ -47,9 +47,10 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const double* __restri
       tr = dd_add(tr, sRed[2 * w]);
       ti = dd_add(ti, sRed[2 * w + 1]);
     }
-    if (mode == 0) {
-      // per = 2 (-1)^(n-1) * sum ; scaling by +-2 is exact
-      const double s = ((n - 1) & 1) ? -2.0 : 2.0;
+    if (mode == 0 || mode == 2) {
+      // mode 0: per = 2 (-1)^(n-1) * sum (halved Glynn form)
+      // mode 2: per = (-1)^n * sum (Eq. ryser2); scaling by +-2 or +-1 is exact
+      const double s = mode == 0 ? (((n - 1) & 1) ? -2.0 : 2.0) : ((n & 1) ? -1.0 : 1.0);
       out[0] = s * __dadd_rn(tr.hi, tr.lo);
       if (cplx) out[1] = s * __dadd_rn(ti.hi, ti.lo);
     } else {

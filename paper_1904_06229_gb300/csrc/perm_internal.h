@@ -72,6 +72,7 @@ int walk_blocks_r64_f32(int n);
 // Fixed-order reduction of per-block dd partials.
 //   mode 0: out = 2 (-1)^(n-1) * sum, rounded to double(s)  (1 or 2 doubles)
 //   mode 1: out = sum as dd                                    (2 or 4 doubles)
+//   mode 2: out = (-1)^n * sum, rounded to double(s)            (Eq. ryser2)
 cudaError_t finalize_launch(const double* partials, int nparts, bool cplx, int n, int mode, double* out,
                             cudaStream_t stream);
 

@@ -39,6 +39,8 @@ EXPORTS = [
     "perm_c128_f32p",
     "perm_f64_f32p",
     "perm_c128_noalloc",
+    "perm_c128_repeated",
+    "perm_c128_band",
     "perm_batch",
     "perm_batch_autotune",
     "perm_mod01",
@@ -80,6 +82,8 @@ def load(path: Optional[str] = None):
             "perm_c128_f32p": [vp, i, vp, vp],
             "perm_f64_f32p": [vp, i, vp, vp],
             "perm_c128_noalloc": [vp, i, vp, vp],
+            "perm_c128_repeated": [vp, vp, i, i, vp, vp],
+            "perm_c128_band": [vp, i, i, i, vp, vp],
             "perm_batch": [vp, vp, i, vp, vp],
             "perm_batch_autotune": [i, i],
             "perm_mod01": [vp, i, vp, vp, vp],
@@ -206,6 +210,41 @@ def perm_c128_noalloc(A: torch.Tensor, out: torch.Tensor, stream=None) -> torch.
     A = _c128(A)
     n = _square(A)
     _check(load().perm_c128_noalloc(_dptr(A), n, _dptr(out), _stream(A, stream)), "perm_c128_noalloc")
+    return out
+
+
+def perm_c128_repeated(Cbar: torch.Tensor, mult: Sequence[int], out: Optional[torch.Tensor] = None,
+                       stream=None) -> torch.Tensor:
+    """Eq.(ryser2): permanent of the matrix whose distinct columns are the
+    columns of the complex128 n x R tensor `Cbar`, column k repeated mult[k]
+    times -> float64 tensor [re, im]."""
+    if Cbar.dtype != torch.complex128 or Cbar.dim() != 2:
+        raise TypeError("complex128 n x R tensor expected")
+    Cbar = Cbar.contiguous()
+    n, R = int(Cbar.shape[0]), int(Cbar.shape[1])
+    if len(mult) != R:
+        raise ValueError("one multiplicity per distinct column")
+    m = (ctypes.c_int * R)(*[int(v) for v in mult])
+    out = _out(out, 2, Cbar)
+    _check(load().perm_c128_repeated(_dptr(Cbar), ctypes.addressof(m), R, n, _dptr(out), _stream(Cbar, stream)),
+           "perm_c128_repeated")
+    return out
+
+
+def perm_c128_band(A: torch.Tensor, k: int, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """App. C band permanent of a complex128 n x n tensor, or of each matrix
+    of a (count, n, n) tensor, with half-bandwidth k -> float64 (count, 2)."""
+    if A.dtype != torch.complex128:
+        raise TypeError("complex128 matrices expected")
+    A = A.contiguous()
+    if A.dim() == 2:
+        A = A.unsqueeze(0)
+    if A.dim() != 3 or A.shape[1] != A.shape[2]:
+        raise ValueError("(count, n, n) or (n, n) expected")
+    count, n = int(A.shape[0]), int(A.shape[1])
+    if out is None:
+        out = torch.empty((count, 2), dtype=torch.float64, device=A.device)
+    _check(load().perm_c128_band(_dptr(A), n, int(k), count, _dptr(out), _stream(A, stream)), "perm_c128_band")
     return out
 
 

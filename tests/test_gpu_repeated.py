@@ -1,0 +1,65 @@
+"""Eq.(ryser2) on the GPU (perm_c128_repeated) against the oracle's plain
+evaluation of Eq.(ryser2), against the Gray-walk permanent of the expanded
+matrix, and on closed forms."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_1904_06229_gb300 import perm as P
+from paper_1904_06229_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+REL = 1e-10
+
+
+def gpu_rep(Cb, mult):
+    o = P.perm_c128_repeated(torch.from_numpy(np.ascontiguousarray(Cb.astype(np.complex128))).cuda(), mult)
+    assert P.perm_last_status() == 0
+    o = o.cpu().numpy()
+    return complex(o[0], o[1])
+
+
+@pytest.mark.parametrize("mult", [[1], [4], [1, 1], [2, 1, 3], [1] * 9, [3, 3, 3, 3], [5, 1, 1, 2, 6],
+                                  [2] * 8, [7, 7, 6]])
+def test_vs_oracle_ryser2(mult):
+    n = sum(mult)
+    Cb = W.haar_submatrix(n, n * n, 300 + n)[:, :len(mult)]
+    r = O.per_repeated(Cb, mult)
+    ref = complex(float(r[0]), float(r[1]))
+    got = gpu_rep(Cb, mult)
+    assert abs(got - ref) <= REL * abs(ref), (got, ref)
+
+
+@pytest.mark.parametrize("mult", [[3, 2, 2, 1, 4, 3, 2, 3, 2, 2], [1] * 24, [6, 6, 6, 6, 6]])
+def test_vs_gray_walk_of_expanded(mult):
+    n = sum(mult)
+    Cb = W.complex_gaussian(n, 7 + n)[:, :len(mult)]
+    A = O.expand_columns(Cb, mult)
+    full = P.perm_c128(torch.from_numpy(A).cuda()).cpu().numpy()
+    ref = complex(full[0], full[1])
+    got = gpu_rep(Cb, mult)
+    assert abs(got - ref) <= REL * abs(ref), (got, ref)
+
+
+def test_closed_forms():
+    for n in (1, 5, 12, 20):
+        assert gpu_rep(np.ones((n, 1)), [n]) == pytest.approx(math.factorial(n), rel=1e-14)
+    c = W.complex_gaussian(10, 4)[:, :1]
+    ref = math.factorial(10) * np.prod(c[:, 0])
+    assert abs(gpu_rep(c, [10]) - ref) <= 1e-13 * abs(ref)
+
+
+def test_errors_and_host_buffers():
+    Cb = W.complex_gaussian(6, 1)[:, :3]
+    with pytest.raises(P.PermError):
+        P.perm_c128_repeated(torch.from_numpy(Cb).cuda(), [2, 2, 1])  # sums to 5, not 6
+    with pytest.raises(P.PermError):
+        P.perm_c128_repeated(torch.from_numpy(Cb).cuda(), [2, 0, 4])
+    host = P.perm_c128_repeated(torch.from_numpy(Cb), [2, 2, 2])
+    torch.cuda.synchronize()
+    assert host.device.type == "cpu"
+    dev = P.perm_c128_repeated(torch.from_numpy(Cb).cuda(), [2, 2, 2]).cpu()
+    assert torch.equal(host, dev)

@@ -236,3 +236,63 @@ def test_condition_number_reported():
     A = W.complex_gaussian(12, 5)
     r = O.per(A)
     assert r[2] >= np.hypot(r[0], r[1])
+
+
+# ---------------------------------------------------------------- Eq.(ryser2)
+@pytest.mark.parametrize("mult", [[1], [3], [2, 1], [1, 1, 1], [2, 2, 1], [4, 1, 2], [1, 3, 1, 2], [5, 5]])
+def test_ryser2_vs_brute_on_expanded(mult):
+    n = sum(mult)
+    Cb = W.complex_gaussian(n, 90 + n)[:, :len(mult)]
+    A = O.expand_columns(Cb, mult)
+    r2 = O.per_repeated(Cb, mult)
+    if n <= 8:
+        er, ei = O.per_brute_exact(A)
+        ref = (np.longdouble(er.numerator) / np.longdouble(er.denominator),
+               np.longdouble(ei.numerator) / np.longdouble(ei.denominator))
+    else:
+        g = O.per(A)
+        ref = (g[0], g[1])
+    assert _ld_rel(r2[0], r2[1], *ref) < 1e-14
+
+
+def test_ryser2_closed_forms():
+    # one distinct column of ones repeated n times: per(J_n) = n!
+    for n in (1, 4, 9, 15):
+        r = O.per_repeated(np.ones((n, 1)), [n])
+        assert _ld_rel(r[0], r[1], math.factorial(n), 0) < 1e-15
+    # one column c repeated n times: per = n! prod_i c_i
+    c = W.complex_gaussian(6, 3)[:, :1]
+    r = O.per_repeated(c, [6])
+    ref = math.factorial(6) * np.prod(c[:, 0])
+    assert abs(complex(float(r[0]), float(r[1])) - ref) < 1e-13 * abs(ref)
+
+
+# ------------------------------------------------------- App. C band-limited
+@pytest.mark.parametrize("n,k", [(1, 0), (4, 0), (5, 1), (7, 2), (8, 3), (8, 7)])
+def test_band_vs_brute(n, k):
+    A = O.band_matrix(n, k, 10 * n + k)
+    br, bi = O.band_permanent_exact(A, k)
+    er, ei = O.per_brute_exact(A)
+    assert (br, bi) == (er, ei)  # both exact rationals
+
+
+@pytest.mark.parametrize("n,k", [(14, 1), (16, 2), (18, 3)])
+def test_band_vs_glynn(n, k):
+    A = O.band_matrix(n, k, 5 + n, kind="real" if k == 2 else "gaussian")
+    br, bi = O.band_permanent_exact(A, k)
+    g = O.per(A)
+    ref = complex(float(g[0]), float(g[1]))
+    assert abs(complex(float(br), float(bi)) - ref) <= 1e-13 * abs(ref)
+
+
+def test_band_tridiagonal_fibonacci():
+    # per of the n x n tridiagonal all-ones matrix is the Fibonacci number F_{n+1}
+    fib = [0, 1]
+    for _ in range(40):
+        fib.append(fib[-1] + fib[-2])
+    for n in (1, 2, 3, 10, 25):
+        A = O.band_matrix(n, 1, 0) * 0
+        i, j = np.indices((n, n))
+        A[np.abs(i - j) <= 1] = 1
+        br, bi = O.band_permanent_exact(A, 1)
+        assert br == fib[n + 1] and bi == 0
