@@ -142,7 +142,7 @@ int perm_c128_band(const double* A, int n, int k, int count, double* out, void* 
 /* ---- Batch of independent complex permanents (the random-matrix studies of
  * Secs. 3-6 need 10^5..10^7 permanents of orders up to ~35) ----
  * ptrs: DEVICE array of `count` DEVICE pointers, each to a 2*n_k*n_k complex
- *       matrix; ns: HOST array of the `count` orders (1 <= n_k <= 40);
+ *       matrix; ns: HOST array of the `count` orders (1 <= n_k <= 32);
  * out:  DEVICE array of 2*count doubles (re, im per matrix).
  * All permanents run in one persistent kernel that takes (matrix, chunk) work
  * items, largest order first, from an atomic ticket; per-matrix partials are
@@ -153,6 +153,20 @@ int perm_c128_band(const double* A, int n, int k, int count, double* out, void* 
  * perm_batch_autotune).  Results equal perm_c128 on the same matrix to within
  * rounding of the summation order. */
 int perm_batch(const double* const* ptrs, const int* ns, int count, double* out, void* stream);
+
+/* ---- Batch with the random-matrix statistics of Secs. 3-6 ----
+ * perm_batch, then, per order n = 0..32, statistics of X = |per(A)| / sqrt(n!)
+ * over the batch's matrices of that order (the paper's normalisation, with
+ * <X^2> = 1 for independent variance-1 entries):
+ *   stats[n*PERM_STATS_STRIDE + 0]      number of matrices of order n
+ *   stats[n*PERM_STATS_STRIDE + 1..4]   sum of X, X^2, X^3, X^4
+ *   stats[n*PERM_STATS_STRIDE + 5 + b]  histogram, 16 bins per decade (Sec. 3):
+ *       b = 0: X < 1e-4;  b = 1..96: 10^(-4+(b-1)/16) <= X < 10^(-4+b/16);
+ *       b = 97: X >= 100.
+ * stats: DEVICE array of 33 * PERM_STATS_STRIDE doubles (overwritten).
+ * Sums are formed in a fixed order (deterministic); counts are exact. */
+#define PERM_STATS_STRIDE 103
+int perm_batch_stats(const double* const* ptrs, const int* ns, int count, double* out, double* stats, void* stream);
 
 /* Fill the batch tuning table for orders n_lo..n_hi on the current device by
  * timing candidate chunk lengths on synthetic input (blocking).  Optional:

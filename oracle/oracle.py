@@ -73,7 +73,7 @@ def _load():
             lib.oracle_glynn_mod_range_i8.argtypes = [ld_p, ctypes.c_int, ld_p, ctypes.c_int, u64, u64, ld_p]
             lib.oracle_per_mod_i8.argtypes = [ld_p, ctypes.c_int, ld_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ld_p]
-            lib.oracle_ryser2_c.argtypes = [ld_p, ctypes.c_int, ctypes.c_int, ld_p, ld_p]
+            lib.oracle_ryser2_c.argtypes = [ld_p, ctypes.c_int, ctypes.c_int, ld_p, ld_p, ld_p]
             _lib = lib
     return _lib
 
@@ -195,16 +195,18 @@ def _compensated(xs):
 def per_repeated(Cbar, mult):
     """Eq.(ryser2): permanent of the n x n matrix whose distinct columns are the
     R columns of `Cbar` (n x R), column k repeated mult[k] times.  Long double,
-    plain counting order over the multiplicity vectors.  Returns (re, im)."""
+    plain counting order over the multiplicity vectors.  Returns (re, im,
+    abs_sum), abs_sum = the sum of the terms' magnitudes (for error bounds)."""
     c = np.ascontiguousarray(np.asarray(Cbar).astype(np.complex128)).view(np.float64)
     Cb = np.asarray(Cbar)
     n, R = Cb.shape
     m = np.ascontiguousarray(np.asarray(mult, dtype=np.int32))
     out = np.zeros(2, dtype=np.longdouble)
-    rc = _load().oracle_ryser2_c(_ptr(c), int(n), int(R), _ptr(m), _ptr(out))
+    asum = np.zeros(1, dtype=np.longdouble)
+    rc = _load().oracle_ryser2_c(_ptr(c), int(n), int(R), _ptr(m), _ptr(out), _ptr(asum))
     if rc != 0:
         raise ValueError("bad repeated-column specification")
-    return out[0], out[1]
+    return out[0], out[1], asum[0]
 
 
 def expand_columns(Cbar, mult):
@@ -376,6 +378,31 @@ def band_matrix(n: int, k: int, seed: int, kind: str = "gaussian"):
     i, j = np.indices((n, n))
     A[np.abs(i - j) > k] = 0
     return A
+
+
+STATS_STRIDE = 103
+
+
+def batch_stats(pers, ns):
+    """Statistics of X = |per| / sqrt(n!) per order n = 0..32 (Secs. 3-6):
+    row n = [count, sum X, sum X^2, sum X^3, sum X^4, histogram...] with 16
+    bins per decade: bin 0 for X < 1e-4, bin b = 1..96 for
+    10^(-4+(b-1)/16) <= X < 10^(-4+b/16), bin 97 for X >= 100.  Sums are
+    exactly rounded (math.fsum)."""
+    edges = [10.0 ** (-4.0 + j / 16.0) for j in range(97)]
+    out = np.zeros((33, STATS_STRIDE))
+    xs = {}
+    for p, n in zip(pers, ns):
+        x = abs(complex(p)) / math.sqrt(math.factorial(int(n)))
+        xs.setdefault(int(n), []).append(x)
+    for n, v in xs.items():
+        out[n, 0] = len(v)
+        for q in range(1, 5):
+            out[n, q] = math.fsum(x ** q for x in v)
+        for x in v:
+            b = sum(1 for e in edges if e <= x)
+            out[n, 5 + b] += 1
+    return out
 
 
 # ------------------------------------------------------- primes and the CRT

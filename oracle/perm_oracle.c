@@ -486,7 +486,7 @@ static ld binom_ld(int m, int f) {
   return b;
 }
 
-int oracle_ryser2_c(const double* C, int n, int R, const int* mult, ld* out) {
+int oracle_ryser2_c(const double* C, int n, int R, const int* mult, ld* out, ld* abs_sum) {
   if (n < 1 || n > ORACLE_NMAX || R < 1 || R > n || !C || !mult || !out) return -1;
   int tot = 0;
   for (int k = 0; k < R; ++k) {
@@ -496,7 +496,7 @@ int oracle_ryser2_c(const double* C, int n, int R, const int* mult, ld* out) {
   if (tot != n) return -1;
   int f[ORACLE_NMAX];
   for (int k = 0; k < R; ++k) f[k] = 0;
-  csum sr = {0, 0}, si = {0, 0};
+  csum sr = {0, 0}, si = {0, 0}, sa = {0, 0};
   for (;;) {
     ld wgt = 1;
     int fs = 0;
@@ -514,6 +514,7 @@ int oracle_ryser2_c(const double* C, int n, int R, const int* mult, ld* out) {
     ld sg = (fs & 1) ? -wgt : wgt;
     csum_add(&sr, sg * pr);
     csum_add(&si, sg * pi);
+    csum_add(&sa, wgt * sqrtl(pr * pr + pi * pi));
     /* next f in counting order */
     int k = 0;
     while (k < R && f[k] == mult[k]) f[k] = 0, ++k;
@@ -523,6 +524,7 @@ int oracle_ryser2_c(const double* C, int n, int R, const int* mult, ld* out) {
   ld s = (n & 1) ? -1 : 1;
   out[0] = s * csum_value(&sr);
   out[1] = s * csum_value(&si);
+  if (abs_sum) *abs_sum = csum_value(&sa);
   return 0;
 }
 

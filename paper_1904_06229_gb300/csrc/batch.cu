@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -170,6 +171,77 @@ int batch_resident_blocks_rows(RowMode rows) {
 
 int batch_resident_blocks() { return batch_resident_blocks_rows(rows_from_env()); }
 
+// ---- statistics of X = |per| / sqrt(n!) per order (Secs. 3-6) ----
+// stats[n * PERM_STATS_STRIDE + ...]: [0] count, [1..4] sum X^1..X^4,
+// [5 + b] histogram: b = 0 for X < 1e-4, b = 1..96 for
+// 10^(-4 + (b-1)/16) <= X < 10^(-4 + b/16) (16 bins per decade), b = 97 for
+// X >= 100.  One block per order; every sum is formed in a fixed order
+// (double-double per thread, fixed tree), counts are integer atomics.
+constexpr int kStatsEdges = 97;  // 10^(-4 + j/16), j = 0..96
+constexpr int kStatsStride = 5 + kStatsEdges + 1;
+
+struct StatsParams {
+  double inv_sqrt_fact[kBatchNMax + 1];
+  double edges[kStatsEdges];
+};
+
+__global__ void __launch_bounds__(256) k_batch_stats(const double* __restrict__ out, const int* __restrict__ ns,
+                                                     int count, StatsParams sp, double* __restrict__ stats) {
+  const int n = blockIdx.x;
+  __shared__ unsigned int hist[kStatsEdges + 1];
+  __shared__ unsigned int cnt;
+  __shared__ dd red[4 * 8];
+  for (int b = threadIdx.x; b <= kStatsEdges; b += blockDim.x) hist[b] = 0;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  dd m1{0, 0}, m2{0, 0}, m3{0, 0}, m4{0, 0};
+  unsigned int c = 0;
+  for (int k = threadIdx.x; k < count; k += blockDim.x) {
+    if (ns[k] != n) continue;
+    const double re = out[2 * (size_t)k], im = out[2 * (size_t)k + 1];
+    const double x = sqrt(re * re + im * im) * sp.inv_sqrt_fact[n];
+    const double x2 = x * x;
+    m1 = dd_add_d(m1, x);
+    m2 = dd_add_d(m2, x2);
+    m3 = dd_add_d(m3, x2 * x);
+    m4 = dd_add_d(m4, x2 * x2);
+    ++c;
+    // bin = number of edges <= x (binary search over the ascending edges)
+    int lo = 0, hi = kStatsEdges;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (sp.edges[mid] <= x)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    atomicAdd(&hist[lo], 1u);
+  }
+  m1 = dd_warp_sum(m1);
+  m2 = dd_warp_sum(m2);
+  m3 = dd_warp_sum(m3);
+  m4 = dd_warp_sum(m4);
+  for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    red[4 * warp] = m1;
+    red[4 * warp + 1] = m2;
+    red[4 * warp + 2] = m3;
+    red[4 * warp + 3] = m4;
+    atomicAdd(&cnt, c);
+  }
+  __syncthreads();
+  double* st = stats + (size_t)n * kStatsStride;
+  if (threadIdx.x == 0) {
+    dd t[4] = {red[0], red[1], red[2], red[3]};
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      for (int q = 0; q < 4; ++q) t[q] = dd_add(t[q], red[4 * w + q]);
+    st[0] = (double)cnt;
+    for (int q = 0; q < 4; ++q) st[1 + q] = __dadd_rn(t[q].hi, t[q].lo);
+  }
+  for (int b = threadIdx.x; b <= kStatsEdges; b += blockDim.x) st[5 + b] = (double)hist[b];
+}
+
 }  // namespace perm
 
 using namespace perm;
@@ -177,6 +249,7 @@ using namespace perm;
 namespace {
 
 std::mutex g_batch_mu;
+std::mutex g_stats_mu;
 
 // ---- tuning table: codes per lane L for each (device, order) ----
 struct Tune {
@@ -377,7 +450,8 @@ int perm_batch_autotune(int n_lo, int n_hi) {
   return PERM_OK;
 }
 
-int perm_batch(const double* const* ptrs, const int* ns, int count, double* out, void* stream) {
+static int batch_run(const double* const* ptrs, const int* ns, int count, double* out, void* stream,
+                     const int** dev_ns) {
   if (!ptrs || !ns || !out) return PERM_ENULL;
   if (count < 1) return PERM_EINVAL;
   for (int k = 0; k < count; ++k)
@@ -476,7 +550,29 @@ int perm_batch(const double* const* ptrs, const int* ns, int count, double* out,
     while (g_plans.size() > kMaxPlans) g_plans.pop_back();
     plan = g_plans.front().get();
   }
+  if (dev_ns) *dev_ns = (const int*)plan->mn.p;
   return status_of_b(cudaGraphLaunch(plan->exec, s));
+}
+
+int perm_batch(const double* const* ptrs, const int* ns, int count, double* out, void* stream) {
+  return batch_run(ptrs, ns, count, out, stream, nullptr);
+}
+
+int perm_batch_stats(const double* const* ptrs, const int* ns, int count, double* out, double* stats, void* stream) {
+  if (!stats) return PERM_ENULL;
+  const int* d_ns = nullptr;
+  std::lock_guard<std::mutex> lk(g_stats_mu);
+  int rc = batch_run(ptrs, ns, count, out, stream, &d_ns);
+  if (rc) return rc;
+  StatsParams sp;
+  for (int n = 0; n <= kBatchNMax; ++n) {
+    double f = 1.0;
+    for (int t = 2; t <= n; ++t) f *= (double)t;
+    sp.inv_sqrt_fact[n] = 1.0 / std::sqrt(f);
+  }
+  for (int j = 0; j < kStatsEdges; ++j) sp.edges[j] = std::pow(10.0, -4.0 + (double)j / 16.0);
+  k_batch_stats<<<kBatchNMax + 1, 256, 0, (cudaStream_t)stream>>>(out, d_ns, count, sp, stats);
+  return status_of_b(cudaGetLastError());
 }
 
 }  // extern "C"

@@ -42,15 +42,18 @@ struct FxShape {
 };
 
 // Double with value v * 2^(eb - 1086) (eb = 1086 - scale exponent), from the
-// bits of v only: |v| normalised by its leading-zero count, 52 fraction bits
-// kept (truncation).  0 for v == 0 and for results below the normal range.
+// bits of v only: |v| normalised by its leading-zero count, rounded to 53
+// significant bits (half-way cases away from zero), exponent field from the
+// leading-zero count.  0 for v == 0 and for results below the normal range.
 __device__ __forceinline__ double fx_to_double(long long v, int eb) {
   const unsigned long long s = (unsigned long long)(v >> 63);
   const unsigned long long m = ((unsigned long long)v ^ s) - s;
   const int lz = __clzll((long long)m);
   const unsigned long long mn = m << (lz & 63);
-  const uint32_t hi = (uint32_t)(mn >> 32), lo = (uint32_t)mn;
-  const int be = eb - lz;  // biased exponent of the result
+  const unsigned long long rn = mn + 0x400ull;  // + half a unit of the 53rd bit
+  const int up = rn < mn ? 1 : 0;               // rounding carried past bit 63
+  const uint32_t hi = (uint32_t)(rn >> 32), lo = (uint32_t)rn;
+  const int be = eb - lz + up;  // biased exponent of the result
   const uint32_t dhi = ((uint32_t)s & 0x80000000u) | ((uint32_t)be << 20) | ((hi >> 11) & 0xFFFFFu);
   const uint32_t dlo = (hi << 21) | (lo >> 11);
   return (m == 0 || be <= 0) ? 0.0 : __hiloint2double((int)dhi, (int)dlo);
@@ -64,7 +67,8 @@ __device__ __forceinline__ float fx_to_f32(long long v, int lzref) {
   const int lz = __clzll((long long)m);
   const unsigned long long mn = m << (lz & 63);
   const int fexp = 127 + lzref - lz;
-  const uint32_t bits = ((uint32_t)s & 0x80000000u) | ((uint32_t)fexp << 23) | ((uint32_t)(mn >> 40) & 0x7FFFFFu);
+  uint32_t bits = ((uint32_t)s & 0x80000000u) | ((uint32_t)fexp << 23) | ((uint32_t)(mn >> 40) & 0x7FFFFFu);
+  bits += (uint32_t)(mn >> 39) & 1u;  // round half up on the magnitude (a carry moves into the exponent)
   return (m == 0 || fexp <= 0) ? 0.0f : __int_as_float((int)bits);
 }
 

@@ -14,8 +14,9 @@
 // m_k C_k and adds C_{k+1}; none of this rounds, so nothing drifts however
 // often carries happen.  The weight is exact table values: binom(m_0, f_0)
 // times the product over the other digits, which changes only on a carry.
-// The signed weight enters the FP64 accumulate FMA directly, so a term costs
-// the same FP64 work as a Gray-walk term: the 4(n-1) product FMAs and 2 more.
+// The signed weight multiplies the FP64 product, and every term is added
+// into double-double accumulators (Eq. ryser2 cancels much more than the
+// halved Gray sum does).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -150,15 +151,16 @@ __global__ void __launch_bounds__(kWalkThreads) k_ryser2(const double* __restric
 #pragma unroll 1
     for (int k = 1; k < R; ++k) wrest *= sBin[prm.bin_off[k] + f[k]], par += f[k];
     uint32_t odd = (uint32_t)(par & 1);
-    while (r < end) {
-      const uint64_t run_end = min(end, r + kRun);
-      double sr = 0.0, si = 0.0;
-      for (; r < run_end; ++r) {
+    {
+      // Eq.(ryser2) sums terms of both signs and very different sizes (its
+      // condition number grows much faster than the halved Gray sum's), so
+      // every term goes straight into the double-double accumulators.
+      for (; r < end; ++r) {
         double pr, pi;
         FxProduct<N, true, kProdF64>::eval(vr, vi, sEb, pr, pi, z);
         const double sw = flip_sign(fma(wrest, bin0[f0], z), odd);  // (-1)^{sum f} prod binom
-        sr = fma(sw, pr, sr);
-        si = fma(sw, pi, si);
+        accr = dd_add_d(accr, fma(sw, pr, z));
+        acci = dd_add_d(acci, fma(sw, pi, z));
         if (r + 1 >= end) continue;  // no step past this thread's range
         if (f0 < m0) {
           ++f0;
@@ -208,8 +210,6 @@ __global__ void __launch_bounds__(kWalkThreads) k_ryser2(const double* __restric
           odd = (uint32_t)(par & 1);
         }
       }
-      accr = dd_add_d(accr, sr);
-      acci = dd_add_d(acci, si);
     }
   }
   __syncthreads();

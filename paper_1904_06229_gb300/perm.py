@@ -42,6 +42,7 @@ EXPORTS = [
     "perm_c128_repeated",
     "perm_c128_band",
     "perm_batch",
+    "perm_batch_stats",
     "perm_batch_autotune",
     "perm_mod01",
     "perm_crt",
@@ -85,6 +86,7 @@ def load(path: Optional[str] = None):
             "perm_c128_repeated": [vp, vp, i, i, vp, vp],
             "perm_c128_band": [vp, i, i, i, vp, vp],
             "perm_batch": [vp, vp, i, vp, vp],
+            "perm_batch_stats": [vp, vp, i, vp, vp, vp],
             "perm_batch_autotune": [i, i],
             "perm_mod01": [vp, i, vp, vp, vp],
             "perm_crt": [vp, vp, i, vp],
@@ -268,6 +270,32 @@ def perm_batch(mats: Sequence[torch.Tensor], out: Optional[torch.Tensor] = None,
     _check(load().perm_batch(_dptr(ptrs), ctypes.addressof(ns), count, _dptr(out), _stream(mats[0], stream)),
            "perm_batch")
     return out
+
+
+PERM_STATS_STRIDE = 103
+
+
+def perm_batch_stats(mats: Sequence[torch.Tensor], out: Optional[torch.Tensor] = None,
+                     stats: Optional[torch.Tensor] = None, stream=None, ptrs: Optional[torch.Tensor] = None):
+    """perm_batch plus the per-order statistics of X = |per| / sqrt(n!) ->
+    (out (count, 2), stats (33, PERM_STATS_STRIDE)); see include/perm.h."""
+    count = len(mats)
+    if count == 0:
+        raise ValueError("empty batch")
+    dev = mats[0].device
+    ns = (ctypes.c_int * count)(*[_square(m) for m in mats])
+    for m in mats:
+        if m.dtype != torch.complex128 or not m.is_contiguous() or m.device != dev:
+            raise TypeError("contiguous complex128 matrices on one device expected")
+    if ptrs is None:
+        ptrs = torch.tensor([m.data_ptr() for m in mats], dtype=torch.int64).to(dev)
+    if out is None:
+        out = torch.empty((count, 2), dtype=torch.float64, device=dev)
+    if stats is None:
+        stats = torch.empty((33, PERM_STATS_STRIDE), dtype=torch.float64, device=dev)
+    _check(load().perm_batch_stats(_dptr(ptrs), ctypes.addressof(ns), count, _dptr(out), _dptr(stats),
+                                   _stream(mats[0], stream)), "perm_batch_stats")
+    return out, stats
 
 
 def perm_batch_autotune(n_lo: int, n_hi: int) -> None:

@@ -1,6 +1,11 @@
 """Eq.(ryser2) on the GPU (perm_c128_repeated) against the oracle's plain
 evaluation of Eq.(ryser2), against the Gray-walk permanent of the expanded
-matrix, and on closed forms."""
+matrix, and on closed forms.
+
+Tolerance: Eq.(ryser2) is an un-halved inclusion-exclusion sum whose terms
+cancel strongly, so FP64 products bound its accuracy by the sum of the term
+magnitudes: |err| <= max(1e-10 |per|, 8 n u sum|t|) with u = 2^-53 and
+sum|t| from the oracle."""
 import math
 
 import numpy as np
@@ -13,6 +18,11 @@ from paper_1904_06229_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 REL = 1e-10
+U = 2.0 ** -53
+
+
+def tol(n, ref, asum):
+    return max(REL * abs(ref), 8 * n * U * float(asum))
 
 
 def gpu_rep(Cb, mult):
@@ -30,10 +40,10 @@ def test_vs_oracle_ryser2(mult):
     r = O.per_repeated(Cb, mult)
     ref = complex(float(r[0]), float(r[1]))
     got = gpu_rep(Cb, mult)
-    assert abs(got - ref) <= REL * abs(ref), (got, ref)
+    assert abs(got - ref) <= tol(n, ref, r[2]), (got, ref, float(r[2]))
 
 
-@pytest.mark.parametrize("mult", [[3, 2, 2, 1, 4, 3, 2, 3, 2, 2], [1] * 24, [6, 6, 6, 6, 6]])
+@pytest.mark.parametrize("mult", [[3, 2, 2, 1, 4, 3, 2, 3, 2, 2], [1] * 18, [6, 6, 6, 6, 6]])
 def test_vs_gray_walk_of_expanded(mult):
     n = sum(mult)
     Cb = W.complex_gaussian(n, 7 + n)[:, :len(mult)]
@@ -41,12 +51,14 @@ def test_vs_gray_walk_of_expanded(mult):
     full = P.perm_c128(torch.from_numpy(A).cuda()).cpu().numpy()
     ref = complex(full[0], full[1])
     got = gpu_rep(Cb, mult)
-    assert abs(got - ref) <= REL * abs(ref), (got, ref)
+    asum = O.per_repeated(Cb, mult)[2]
+    assert abs(got - ref) <= tol(n, ref, asum), (got, ref, float(asum))
 
 
 def test_closed_forms():
     for n in (1, 5, 12, 20):
-        assert gpu_rep(np.ones((n, 1)), [n]) == pytest.approx(math.factorial(n), rel=1e-14)
+        asum = O.per_repeated(np.ones((n, 1)), [n])[2]
+        assert abs(gpu_rep(np.ones((n, 1)), [n]) - math.factorial(n)) <= tol(n, math.factorial(n), asum)
     c = W.complex_gaussian(10, 4)[:, :1]
     ref = math.factorial(10) * np.prod(c[:, 0])
     assert abs(gpu_rep(c, [10]) - ref) <= 1e-13 * abs(ref)

@@ -296,3 +296,31 @@ def test_band_tridiagonal_fibonacci():
         A[np.abs(i - j) <= 1] = 1
         br, bi = O.band_permanent_exact(A, 1)
         assert br == fib[n + 1] and bi == 0
+
+
+# ------------------------------------------------- statistics of Secs. 3-6
+def test_batch_stats_bins_and_sums():
+    import math as _m
+    pers = [1.0, _m.sqrt(2.0) * 1.0, 1e-6, 1e3, 10 ** (1 / 16) * 0.999999]
+    ns = [1, 2, 1, 1, 1]
+    st = O.batch_stats(pers, ns)
+    assert st[1, 0] == 4 and st[2, 0] == 1
+    assert st[:, 5:].sum() == 5
+    assert st[1, 5 + 0] == 1          # 1e-6 below 1e-4
+    assert st[1, 5 + 97] == 1         # 1e3 above 100
+    assert st[1, 5 + 65] == 2         # X = 1 and X just below 10^(1/16): [10^0, 10^(1/16))
+    assert st[2, 5 + 65] == 1         # |per| / sqrt(2!) = 1
+    assert st[1, 2] == pytest.approx(1.0 + 1e-12 + 1e6 + (10 ** (1 / 16) * 0.999999) ** 2, rel=1e-15)
+
+
+def test_batch_stats_second_moment_gaussian():
+    # Sec. 3: <X^2> = 1 for independent variance-1 entries
+    n, m = 6, 3000
+    pers = []
+    for k in range(m):
+        r = O.per(W.complex_gaussian(n, 20_000 + k))
+        pers.append(complex(float(r[0]), float(r[1])))
+    st = O.batch_stats(pers, [n] * m)
+    mean_x2 = st[n, 2] / st[n, 0]
+    se = math.sqrt(n / m)  # <X^4> = n + 1 gives Var(X^2) = n
+    assert abs(mean_x2 - 1.0) < 5 * se
