@@ -139,6 +139,23 @@ int perm_c128_repeated(const double* C, const int* mult, int R, int n, double* o
  * order (deterministic). */
 int perm_c128_band(const double* A, int n, int k, int count, double* out, void* stream);
 
+/* ---- Sparse matrices: Ryser's sum restricted to dominating column sets
+ * (Sec. 2.D, App. B "sparsepermanent" / "greedypartition") ----
+ * A product prod_i sum_{j in J} a_ij is zero unless J meets the non-zero
+ * columns of every row.  The greedy partition {S_1..S_d, T} of App. B (rows
+ * of least out-degree first; best of 16 randomised tie-breaks by the number of
+ * sets) restricts the sum to J = (non-empty subset of each S_l) u (any subset
+ * of T): 2^|T| prod (2^|S_l| - 1) sets instead of 2^n.
+ * A: complex n x n (interleaved, row-major), device or host; its non-zero
+ * pattern is read on the host, so for a device A the call waits for `stream`
+ * before returning (the walk itself is asynchronous).  n: 1..64.  out: 2
+ * doubles.  PERM_EINVAL if the partition still has 2^63 sets or more. */
+int perm_c128_sparse(const double* A, int n, double* out, void* stream);
+
+/* The partition perm_c128_sparse uses, on the host (no GPU): block[j] = l for
+ * column j in S_l, -1 for j in T; *count = number of sets (0 if >= 2^63). */
+int perm_sparse_partition(const double* A_host, int n, int* block, uint64_t* count);
+
 /* ---- Batch of independent complex permanents (the random-matrix studies of
  * Secs. 3-6 need 10^5..10^7 permanents of orders up to ~35) ----
  * ptrs: DEVICE array of `count` DEVICE pointers, each to a 2*n_k*n_k complex

@@ -74,6 +74,7 @@ def _load():
             lib.oracle_per_mod_i8.argtypes = [ld_p, ctypes.c_int, ld_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ld_p]
             lib.oracle_ryser2_c.argtypes = [ld_p, ctypes.c_int, ctypes.c_int, ld_p, ld_p, ld_p]
+            lib.oracle_sparse_c.argtypes = [ld_p, ctypes.c_int, ld_p, ld_p, ld_p]
             _lib = lib
     return _lib
 
@@ -378,6 +379,74 @@ def band_matrix(n: int, k: int, seed: int, kind: str = "gaussian"):
     i, j = np.indices((n, n))
     A[np.abs(i - j) > k] = 0
     return A
+
+
+def greedy_partition(A, rng=None):
+    """App. B "greedypartition(A, D)": b_ij = [a_ij != 0]; repeatedly take a
+    row k of least out-degree among the rows left in V (ties: the first, or a
+    random one when `rng` is given), make S_d = N_k (the columns of its
+    non-zeros), remove k and every row whose neighbourhood meets N_k from V;
+    T = the columns in no S_l.  Returns block[j] = l for j in S_l, -1 for T."""
+    A = np.asarray(A)
+    n = A.shape[0]
+    b = (A != 0)
+    deg = b.sum(axis=1)
+    nbr = [set(np.nonzero(b[i])[0].tolist()) for i in range(n)]
+    V = set(range(n))
+    blocks = []
+    while V:
+        dmin = min(deg[i] for i in V)
+        cands = sorted(i for i in V if deg[i] == dmin)
+        k = cands[0] if rng is None else cands[int(rng.integers(len(cands)))]
+        Nk = nbr[k]
+        blocks.append(sorted(Nk))
+        V.discard(k)
+        for l in list(V):
+            if Nk & nbr[l]:
+                V.discard(l)
+    block = [-1] * n
+    for l, S in enumerate(blocks):
+        for j in S:
+            block[j] = l
+    return block
+
+
+def partition_count(block) -> int:
+    """Number of sets the restricted sum visits: 2^|T| prod_l (2^|S_l| - 1)."""
+    from collections import Counter
+
+    c = Counter(block)
+    tot = 1 << c.get(-1, 0)
+    for l, s in c.items():
+        if l >= 0:
+            tot *= (1 << s) - 1
+    return tot
+
+
+def per_sparse(A, block=None):
+    """App. B "sparsepermanent" with the partition `block` (default: the
+    deterministic greedy partition).  Returns (re, im, abs_sum), long double."""
+    a = _as_c128(A)
+    n = a.shape[0]
+    if block is None:
+        block = greedy_partition(A)
+    bl = np.ascontiguousarray(np.asarray(block, dtype=np.int32))
+    out = np.zeros(2, dtype=np.longdouble)
+    asum = np.zeros(1, dtype=np.longdouble)
+    rc = _load().oracle_sparse_c(_ptr(a), n, _ptr(bl), _ptr(out), _ptr(asum))
+    if rc != 0:
+        raise ValueError("bad sparse partition")
+    return out[0], out[1], asum[0]
+
+
+def sparse_matrix(n: int, p: float, seed: int):
+    """App. B timing study: identity plus Bernoulli(p) off-diagonal entries,
+    here with complex Gaussian values on the non-zero pattern."""
+    rng = np.random.default_rng(seed)
+    mask = rng.random((n, n)) < p
+    np.fill_diagonal(mask, True)
+    vals = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) * np.sqrt(0.5)
+    return np.where(mask, vals, 0).astype(np.complex128)
 
 
 STATS_STRIDE = 103

@@ -27,6 +27,10 @@
  *   oracle_ryser2_c      Eq.(ryser2): the weighted Ryser sum for a matrix with
  *                        repeated columns, over all multiplicity vectors f,
  *                        row sums formed from scratch for every f.
+ *   oracle_sparse_c      App. B "sparsepermanent": Ryser's sum restricted to
+ *                        the sets J that meet every block S_l of a partition
+ *                        {S_1..S_d, T} (non-empty subset of each S_l, any
+ *                        subset of T), row sums formed from scratch.
  *
  * Real matrices are complex matrices with zero imaginary part; every function
  * takes an interleaved (re, im) row-major n x n array of doubles.
@@ -522,6 +526,68 @@ int oracle_ryser2_c(const double* C, int n, int R, const int* mult, ld* out, ld*
     ++f[k];
   }
   ld s = (n & 1) ? -1 : 1;
+  out[0] = s * csum_value(&sr);
+  out[1] = s * csum_value(&si);
+  if (abs_sum) *abs_sum = csum_value(&sa);
+  return 0;
+}
+
+/* ---- App. B "sparsepermanent(A, D, p)".  block[j] = l (0-based block index
+ * of column j) for j in some S_l, or -1 for j in T.  The nested loops of the
+ * listing ("for all non-empty s_l in S_l ... for all t in T") are run as one
+ * mixed-radix counter whose digits are the bitmasks of s_1..s_d (1 .. 2^|S_l|-1)
+ * and of t (0 .. 2^|T|-1). */
+int oracle_sparse_c(const double* A, int n, const int* block, ld* out, ld* abs_sum) {
+  if (n < 1 || n > 40 || !A || !block || !out) return -1;
+  int d = 0;
+  for (int j = 0; j < n; ++j) {
+    if (block[j] < -1) return -1;
+    if (block[j] + 1 > d) d = block[j] + 1;
+  }
+  /* column lists: digit 0..d-1 = blocks, digit d = T */
+  int cols[ORACLE_NMAX + 1][ORACLE_NMAX], ncol[ORACLE_NMAX + 1];
+  for (int l = 0; l <= d; ++l) ncol[l] = 0;
+  for (int j = 0; j < n; ++j) {
+    const int l = block[j] < 0 ? d : block[j];
+    cols[l][ncol[l]++] = j;
+  }
+  for (int l = 0; l < d; ++l)
+    if (ncol[l] == 0) return -1; /* every S_l is non-empty */
+  uint64_t sub[ORACLE_NMAX + 1];
+  for (int l = 0; l < d; ++l) sub[l] = 1; /* smallest non-empty subset */
+  sub[d] = 0;
+  csum sr = {0, 0}, si = {0, 0}, sa = {0, 0};
+  for (;;) {
+    /* J = s_1 u ... u s_d u t */
+    int inJ[ORACLE_NMAX] = {0}, size = 0;
+    for (int l = 0; l <= d; ++l)
+      for (int b = 0; b < ncol[l]; ++b)
+        if ((sub[l] >> b) & 1) inJ[cols[l][b]] = 1, ++size;
+    ld pr = 1, pi = 0;
+    for (int i = 0; i < n; ++i) {
+      ld rr = 0, ri = 0;
+      for (int j = 0; j < n; ++j)
+        if (inJ[j]) rr += RE(A, n, i, j), ri += IM(A, n, i, j);
+      ld nr = pr * rr - pi * ri, ni = pr * ri + pi * rr;
+      pr = nr, pi = ni;
+    }
+    const ld sg = (size & 1) ? -1 : 1;
+    csum_add(&sr, sg * pr);
+    csum_add(&si, sg * pi);
+    csum_add(&sa, sqrtl(pr * pr + pi * pi));
+    /* next combination */
+    int l = 0;
+    for (; l <= d; ++l) {
+      const uint64_t top = (1ull << ncol[l]) - 1;
+      if (sub[l] < top) {
+        ++sub[l];
+        break;
+      }
+      sub[l] = l < d ? 1 : 0;
+    }
+    if (l > d) break;
+  }
+  const ld s = (n & 1) ? -1 : 1;
   out[0] = s * csum_value(&sr);
   out[1] = s * csum_value(&si);
   if (abs_sum) *abs_sum = csum_value(&sa);

@@ -37,6 +37,7 @@ SOURCES = [
     "glynn_mod.cu",
     "ryser2.cu",
     "band.cu",
+    "sparse.cu",
     "batch.cu",
     "perm_abi.cu",
     "peak.cu",

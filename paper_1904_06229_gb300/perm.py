@@ -41,6 +41,8 @@ EXPORTS = [
     "perm_c128_noalloc",
     "perm_c128_repeated",
     "perm_c128_band",
+    "perm_c128_sparse",
+    "perm_sparse_partition",
     "perm_batch",
     "perm_batch_stats",
     "perm_batch_autotune",
@@ -85,6 +87,8 @@ def load(path: Optional[str] = None):
             "perm_c128_noalloc": [vp, i, vp, vp],
             "perm_c128_repeated": [vp, vp, i, i, vp, vp],
             "perm_c128_band": [vp, i, i, i, vp, vp],
+            "perm_c128_sparse": [vp, i, vp, vp],
+            "perm_sparse_partition": [vp, i, vp, vp],
             "perm_batch": [vp, vp, i, vp, vp],
             "perm_batch_stats": [vp, vp, i, vp, vp, vp],
             "perm_batch_autotune": [i, i],
@@ -248,6 +252,29 @@ def perm_c128_band(A: torch.Tensor, k: int, out: Optional[torch.Tensor] = None, 
         out = torch.empty((count, 2), dtype=torch.float64, device=A.device)
     _check(load().perm_c128_band(_dptr(A), n, int(k), count, _dptr(out), _stream(A, stream)), "perm_c128_band")
     return out
+
+
+def perm_c128_sparse(A: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """App. B sparse permanent of a complex128 n x n tensor -> float64 [re, im]."""
+    A = _c128(A)
+    n = _square(A)
+    out = _out(out, 2, A)
+    _check(load().perm_c128_sparse(_dptr(A), n, _dptr(out), _stream(A, stream)), "perm_c128_sparse")
+    return out
+
+
+def perm_sparse_partition(A) -> tuple:
+    """(block list, number of sets) of the partition perm_c128_sparse uses;
+    A is a host complex128 n x n array or tensor."""
+    import numpy as np
+
+    a = np.ascontiguousarray(np.asarray(A.cpu() if isinstance(A, torch.Tensor) else A, dtype=np.complex128))
+    n = a.shape[0]
+    block = (ctypes.c_int * n)()
+    count = ctypes.c_uint64(0)
+    _check(load().perm_sparse_partition(a.ctypes.data, n, ctypes.addressof(block), ctypes.addressof(count)),
+           "perm_sparse_partition")
+    return [int(v) for v in block], int(count.value)
 
 
 def perm_batch(mats: Sequence[torch.Tensor], out: Optional[torch.Tensor] = None, stream=None,

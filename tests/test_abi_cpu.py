@@ -112,3 +112,27 @@ def test_no_cpu_fallback_without_device(lib):
     assert lib.perm_last_status(None) == -3
     v = ctypes.c_double()
     assert lib.perm_fp64_peak(ctypes.addressof(v)) == -3
+
+
+def test_sparse_partition_host(lib):
+    """The library's greedy partition (host-only): pairwise-disjoint row
+    neighbourhoods, the App. B set count, never worse than the first-choice
+    greedy pass of the oracle's independent implementation."""
+    import math
+
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_1904_06229_gb300 import perm
+
+    for n, p, seed in ((30, 0.05, 1), (48, 0.02, 2), (64, 0.005, 3), (5, 0.9, 4)):
+        A = O.sparse_matrix(n, p, seed)
+        block, count = perm.perm_sparse_partition(A)
+        nb = max(block) + 1
+        rows = [set(np.nonzero(A[i])[0].tolist()) for i in range(n)]
+        for l in range(nb):
+            S = {j for j in range(n) if block[j] == l}
+            assert S and S in rows
+        assert count == O.partition_count(block)
+        assert count <= O.partition_count(O.greedy_partition(A))
+        assert math.log2(count) <= n

@@ -324,3 +324,40 @@ def test_batch_stats_second_moment_gaussian():
     mean_x2 = st[n, 2] / st[n, 0]
     se = math.sqrt(n / m)  # <X^4> = n + 1 gives Var(X^2) = n
     assert abs(mean_x2 - 1.0) < 5 * se
+
+
+# ------------------------------------------------------ App. B sparse matrices
+@pytest.mark.parametrize("n,p,seed", [(6, 0.2, 1), (8, 0.1, 2), (12, 0.1, 3), (16, 0.05, 4), (18, 0.15, 5)])
+def test_sparse_vs_glynn(n, p, seed):
+    A = O.sparse_matrix(n, p, seed)
+    block = O.greedy_partition(A)
+    assert O.partition_count(block) <= 1 << n
+    r = O.per_sparse(A, block)
+    g = O.per(A)
+    ref = complex(float(g[0]), float(g[1]))
+    got = complex(float(r[0]), float(r[1]))
+    assert abs(got - ref) <= 1e-13 * abs(ref) + 64 * n * _u_ld() * float(r[2])
+    if n <= 8:
+        er, ei = O.per_brute_exact(A)
+        assert abs(got - complex(float(er), float(ei))) <= 1e-13 * abs(ref)
+
+
+def test_sparse_partition_properties():
+    A = O.sparse_matrix(30, 0.05, 9)
+    rng = np.random.default_rng(0)
+    for block in (O.greedy_partition(A), O.greedy_partition(A, rng)):
+        nb = max(block) + 1
+        # blocks are neighbourhoods of rows, pairwise disjoint by construction
+        for l in range(nb):
+            S = {j for j in range(30) if block[j] == l}
+            assert any(S == set(np.nonzero(A[i])[0].tolist()) for i in range(30))
+        assert O.partition_count(block) < 1 << 30
+
+
+def test_sparse_identity_and_permutation():
+    for n in (1, 5, 11):
+        r = O.per_sparse(np.eye(n, dtype=complex))
+        assert complex(float(r[0]), float(r[1])) == 1
+    P = np.eye(9, dtype=complex)[np.random.default_rng(2).permutation(9)] * 2.0
+    r = O.per_sparse(P)
+    assert complex(float(r[0]), float(r[1])) == 2.0 ** 9
