@@ -316,6 +316,7 @@ def run_gpu(args):
     if rank == 0 and not args.no_extras:
         line["exact"] = exact_measure(P, torch, dev)
         line["precision"] = precision_measure(P, torch, dev)
+        line["next_rows"] = next_rows_measure(P, torch, dev)
     if rank == 0 and not args.no_cpu_baseline:
         cb, (first, count, g) = cpu_oracle_sample(A)
         line["cpu_baseline"] = cb
@@ -382,6 +383,38 @@ def precision_measure(P, torch, dev):
     t32, r32 = _timed(torch, lambda: P.perm_f64_f32p(Bd).cpu())
     out["pm1_n30"] = {"exact": str(exact), "fp64_rel_err": abs(float(r64[0]) - exact) / abs(exact),
                       "f32p_rel_err": abs(float(r32[0]) - exact) / abs(exact), "fp64_s": t64, "f32p_s": t32}
+    return out
+
+
+def next_rows_measure(P, torch, dev):
+    """The widened rows: repeated columns (Eq. ryser2), sparse (App. B) and
+    band-limited (App. C) permanents, each against the dense Gray walk where
+    that is feasible."""
+    from paper_1904_06229_gb300 import workloads as W
+
+    out = {}
+    # Boson-sampling-like output with collisions: 15 modes with two photons each (n = 30)
+    Cb = W.haar_submatrix(30, 900, 30)[:, :15]
+    mult = [2] * 15
+    A = np.concatenate([np.repeat(Cb[:, k:k + 1], 2, axis=1) for k in range(15)], axis=1)
+    tC = torch.from_numpy(np.ascontiguousarray(Cb)).to(dev)
+    tA = torch.from_numpy(np.ascontiguousarray(A)).to(dev)
+    t_rep, r_rep = _timed(torch, lambda: P.perm_c128_repeated(tC, mult).cpu())
+    t_den, r_den = _timed(torch, lambda: P.perm_c128(tA).cpu())
+    a, b = complex(*r_rep.tolist()), complex(*r_den.tolist())
+    out["repeated_n30_2x15"] = {"terms": 3 ** 15, "seconds": t_rep, "dense_codes": 1 << 29, "dense_seconds": t_den,
+                                "speedup": t_den / t_rep, "rel_diff_vs_dense": abs(a - b) / abs(b)}
+    # sparse: identity + Bernoulli(0.02) off-diagonal, n = 48
+    S = W.sparse_matrix(48, 0.02, 48)
+    block, count = P.perm_sparse_partition(S)
+    tS = torch.from_numpy(S).to(dev)
+    t_sp, _ = _timed(torch, lambda: P.perm_c128_sparse(tS).cpu())
+    out["sparse_n48_p0.02"] = {"sets": count, "dense_codes": 1 << 47, "seconds": t_sp, "sets_per_s": count / t_sp}
+    # band: 1000 real-Gaussian band matrices, n = 100, k = 5 (App. C study sizes)
+    Bm = np.stack([W.band_matrix(100, 5, s, kind="real") for s in range(1000)])
+    tB = torch.from_numpy(Bm).to(dev)
+    t_b, _ = _timed(torch, lambda: P.perm_c128_band(tB, 5).cpu())
+    out["band_n100_k5_x1000"] = {"seconds": t_b, "matrices_per_s": 1000 / t_b}
     return out
 
 

@@ -210,12 +210,6 @@ def per_repeated(Cbar, mult):
     return out[0], out[1], asum[0]
 
 
-def expand_columns(Cbar, mult):
-    """The n x n matrix with column k of Cbar repeated mult[k] times."""
-    Cb = np.asarray(Cbar)
-    return np.concatenate([np.repeat(Cb[:, k:k + 1], int(mk), axis=1) for k, mk in enumerate(mult)], axis=1)
-
-
 # ------------------------------------------------------------------- integers
 def _limbs_to_int(limbs) -> int:
     v = 0
@@ -368,19 +362,6 @@ def band_permanent_exact(A, k: int):
     return sr, si
 
 
-def band_matrix(n: int, k: int, seed: int, kind: str = "gaussian"):
-    """Random complex band matrix (zero outside |i - j| <= k); the App. C
-    timing study uses real Gaussian entries (kind='real')."""
-    rng = np.random.default_rng(seed)
-    if kind == "real":
-        A = rng.standard_normal((n, n)).astype(np.complex128)
-    else:
-        A = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) * np.sqrt(0.5)
-    i, j = np.indices((n, n))
-    A[np.abs(i - j) > k] = 0
-    return A
-
-
 def greedy_partition(A, rng=None):
     """App. B "greedypartition(A, D)": b_ij = [a_ij != 0]; repeatedly take a
     row k of least out-degree among the rows left in V (ties: the first, or a
@@ -437,16 +418,6 @@ def per_sparse(A, block=None):
     if rc != 0:
         raise ValueError("bad sparse partition")
     return out[0], out[1], asum[0]
-
-
-def sparse_matrix(n: int, p: float, seed: int):
-    """App. B timing study: identity plus Bernoulli(p) off-diagonal entries,
-    here with complex Gaussian values on the non-zero pattern."""
-    rng = np.random.default_rng(seed)
-    mask = rng.random((n, n)) < p
-    np.fill_diagonal(mask, True)
-    vals = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) * np.sqrt(0.5)
-    return np.where(mask, vals, 0).astype(np.complex128)
 
 
 STATS_STRIDE = 103

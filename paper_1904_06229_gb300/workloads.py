@@ -19,6 +19,11 @@ Generators (paper sections they follow):
   zero_one          0-1 entries with a given density.
   batch_study       the many-matrix study: n ~ U{n_lo..n_hi}, alternating
                     Gaussian / Haar (m = n^2) members, shuffled order.
+  sparse_matrix     Sec. 2.D / App. B timing family: identity plus
+                    Bernoulli(p) off-diagonal non-zeros (complex Gaussian values).
+  band_matrix       Sec. 2.D / App. C: zero outside |i - j| <= k.
+  expand_columns    the n x n matrix with column k of a given n x R matrix
+                    repeated mult[k] times (Eq. ryser2 inputs).
 All draws use numpy's PCG64 (`numpy.random.default_rng(seed)`).
 """
 from __future__ import annotations
@@ -90,3 +95,29 @@ def batch_study(count: int, seed: int = 3, n_lo: int = 12, n_hi: int = 28):
             mats.append(haar_submatrix(n, n * n, sub))
     order = rng.permutation(count)
     return ns[order], [mats[i] for i in order]
+
+
+def sparse_matrix(n: int, p: float, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    mask = rng.random((n, n)) < p
+    np.fill_diagonal(mask, True)
+    vals = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) * np.sqrt(0.5)
+    return np.where(mask, vals, 0).astype(np.complex128)
+
+
+def band_matrix(n: int, k: int, seed: int, kind: str = "gaussian") -> np.ndarray:
+    """Random band matrix; kind='real' gives real N(0,1) entries (the App. C
+    timing study), otherwise complex Gaussian."""
+    rng = np.random.default_rng(seed)
+    if kind == "real":
+        A = rng.standard_normal((n, n)).astype(np.complex128)
+    else:
+        A = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) * np.sqrt(0.5)
+    i, j = np.indices((n, n))
+    A[np.abs(i - j) > k] = 0
+    return A
+
+
+def expand_columns(Cbar, mult) -> np.ndarray:
+    Cb = np.asarray(Cbar)
+    return np.concatenate([np.repeat(Cb[:, k:k + 1], int(mk), axis=1) for k, mk in enumerate(mult)], axis=1)

@@ -124,9 +124,10 @@ def test_sparse_partition_host(lib):
 
     from oracle import oracle as O
     from paper_1904_06229_gb300 import perm
+    from paper_1904_06229_gb300 import workloads as W
 
     for n, p, seed in ((30, 0.05, 1), (48, 0.02, 2), (64, 0.005, 3), (5, 0.9, 4)):
-        A = O.sparse_matrix(n, p, seed)
+        A = W.sparse_matrix(n, p, seed)
         block, count = perm.perm_sparse_partition(A)
         nb = max(block) + 1
         rows = [set(np.nonzero(A[i])[0].tolist()) for i in range(n)]

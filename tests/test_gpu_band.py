@@ -6,6 +6,7 @@ import pytest
 import torch
 
 from oracle import oracle as O
+from paper_1904_06229_gb300 import workloads as W
 from paper_1904_06229_gb300 import perm as P
 
 pytestmark = pytest.mark.gpu
@@ -22,7 +23,7 @@ def gpu_band(A, k):
 @pytest.mark.parametrize("n,k", [(1, 0), (1, 3), (3, 0), (6, 1), (9, 2), (12, 3), (14, 4), (16, 5), (30, 2),
                                  (40, 5)])
 def test_vs_exact_oracle(n, k):
-    A = O.band_matrix(n, k, 77 + n + k)
+    A = W.band_matrix(n, k, 77 + n + k)
     br, bi = O.band_permanent_exact(A, k)
     ref = complex(float(br), float(bi))
     got = gpu_band(A, k)[0]
@@ -31,7 +32,7 @@ def test_vs_exact_oracle(n, k):
 
 @pytest.mark.parametrize("n,k", [(20, 3), (24, 5)])
 def test_vs_gray_walk(n, k):
-    A = O.band_matrix(n, k, n * k, kind="real")
+    A = W.band_matrix(n, k, n * k, kind="real")
     full = P.perm_c128(torch.from_numpy(A).cuda()).cpu().numpy()
     ref = complex(full[0], full[1])
     assert abs(gpu_band(A, k)[0] - ref) <= REL * abs(ref)
@@ -48,7 +49,7 @@ def test_fibonacci_and_batch():
         got = gpu_band(mats[-1], 1)[0]
         assert got == pytest.approx(fib[n + 1], rel=1e-14)
     # a batch of equal-size band matrices in one launch
-    stack = np.stack([O.band_matrix(33, 4, s) for s in range(5)])
+    stack = np.stack([W.band_matrix(33, 4, s) for s in range(5)])
     out = gpu_band(stack, 4)
     for s in range(5):
         br, bi = O.band_permanent_exact(stack[s], 4)
@@ -61,7 +62,7 @@ def test_long_band_matrix_runs():
     and compare with the product of the halves' permanents (block diagonal).
     Entries are scaled by 0.4 to keep |per| far from the double range limits."""
     n, h = 400, 200
-    A = O.band_matrix(n, 5, 5) * 0.4
+    A = W.band_matrix(n, 5, 5) * 0.4
     A[h - 5:h, h:h + 5] = 0
     A[h:h + 5, h - 5:h] = 0
     whole = gpu_band(A, 5)[0]

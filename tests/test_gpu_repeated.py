@@ -47,7 +47,7 @@ def test_vs_oracle_ryser2(mult):
 def test_vs_gray_walk_of_expanded(mult):
     n = sum(mult)
     Cb = W.complex_gaussian(n, 7 + n)[:, :len(mult)]
-    A = O.expand_columns(Cb, mult)
+    A = W.expand_columns(Cb, mult)
     full = P.perm_c128(torch.from_numpy(A).cuda()).cpu().numpy()
     ref = complex(full[0], full[1])
     got = gpu_rep(Cb, mult)

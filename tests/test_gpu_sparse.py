@@ -6,6 +6,7 @@ import pytest
 import torch
 
 from oracle import oracle as O
+from paper_1904_06229_gb300 import workloads as W
 from paper_1904_06229_gb300 import perm as P
 
 pytestmark = pytest.mark.gpu
@@ -22,7 +23,7 @@ def gpu_sparse(A):
 @pytest.mark.parametrize("n,p,seed", [(1, 0.5, 1), (4, 0.3, 2), (9, 0.2, 3), (13, 0.1, 4), (16, 0.1, 5),
                                       (18, 0.05, 6)])
 def test_vs_oracle_sparse(n, p, seed):
-    A = O.sparse_matrix(n, p, seed)
+    A = W.sparse_matrix(n, p, seed)
     r = O.per_sparse(A)  # the oracle's own partition: any valid partition gives per(A)
     ref = complex(float(r[0]), float(r[1]))
     got = gpu_sparse(A)
@@ -31,14 +32,14 @@ def test_vs_oracle_sparse(n, p, seed):
 
 @pytest.mark.parametrize("n,p,seed", [(20, 0.1, 7), (24, 0.08, 8)])
 def test_vs_glynn_oracle(n, p, seed):
-    A = O.sparse_matrix(n, p, seed)
+    A = W.sparse_matrix(n, p, seed)
     g = O.per(A)
     ref = complex(float(g[0]), float(g[1]))
     assert abs(gpu_sparse(A) - ref) <= 1e-9 * abs(ref)
 
 
 def test_vs_dense_walk_n32():
-    A = O.sparse_matrix(32, 0.04, 32)
+    A = W.sparse_matrix(32, 0.04, 32)
     d = P.perm_c128(torch.from_numpy(A).cuda()).cpu().numpy()
     ref = complex(d[0], d[1])
     assert abs(gpu_sparse(A) - ref) <= 1e-9 * abs(ref)
@@ -48,8 +49,8 @@ def test_identity_permutation_and_blocks():
     assert gpu_sparse(np.eye(20, dtype=complex)) == 1
     Pm = np.eye(30, dtype=complex)[np.random.default_rng(4).permutation(30)]
     assert gpu_sparse(Pm) == 1
-    B = O.sparse_matrix(12, 0.2, 1)
-    C = O.sparse_matrix(11, 0.2, 2)
+    B = W.sparse_matrix(12, 0.2, 1)
+    C = W.sparse_matrix(11, 0.2, 2)
     M = np.zeros((23, 23), dtype=complex)
     M[:12, :12] = B
     M[12:, 12:] = C
@@ -60,7 +61,7 @@ def test_identity_permutation_and_blocks():
 
 def test_large_sparse_runs():
     """n = 48, p = 0.02: 2^25 sets instead of 2^47."""
-    A = O.sparse_matrix(48, 0.02, 48)
+    A = W.sparse_matrix(48, 0.02, 48)
     block, count = P.perm_sparse_partition(A)
     assert 0 < count < 1 << 30
     v = gpu_sparse(A)

@@ -243,7 +243,7 @@ def test_condition_number_reported():
 def test_ryser2_vs_brute_on_expanded(mult):
     n = sum(mult)
     Cb = W.complex_gaussian(n, 90 + n)[:, :len(mult)]
-    A = O.expand_columns(Cb, mult)
+    A = W.expand_columns(Cb, mult)
     r2 = O.per_repeated(Cb, mult)
     if n <= 8:
         er, ei = O.per_brute_exact(A)
@@ -270,7 +270,7 @@ def test_ryser2_closed_forms():
 # ------------------------------------------------------- App. C band-limited
 @pytest.mark.parametrize("n,k", [(1, 0), (4, 0), (5, 1), (7, 2), (8, 3), (8, 7)])
 def test_band_vs_brute(n, k):
-    A = O.band_matrix(n, k, 10 * n + k)
+    A = W.band_matrix(n, k, 10 * n + k)
     br, bi = O.band_permanent_exact(A, k)
     er, ei = O.per_brute_exact(A)
     assert (br, bi) == (er, ei)  # both exact rationals
@@ -278,7 +278,7 @@ def test_band_vs_brute(n, k):
 
 @pytest.mark.parametrize("n,k", [(14, 1), (16, 2), (18, 3)])
 def test_band_vs_glynn(n, k):
-    A = O.band_matrix(n, k, 5 + n, kind="real" if k == 2 else "gaussian")
+    A = W.band_matrix(n, k, 5 + n, kind="real" if k == 2 else "gaussian")
     br, bi = O.band_permanent_exact(A, k)
     g = O.per(A)
     ref = complex(float(g[0]), float(g[1]))
@@ -291,7 +291,7 @@ def test_band_tridiagonal_fibonacci():
     for _ in range(40):
         fib.append(fib[-1] + fib[-2])
     for n in (1, 2, 3, 10, 25):
-        A = O.band_matrix(n, 1, 0) * 0
+        A = W.band_matrix(n, 1, 0) * 0
         i, j = np.indices((n, n))
         A[np.abs(i - j) <= 1] = 1
         br, bi = O.band_permanent_exact(A, 1)
@@ -329,7 +329,7 @@ def test_batch_stats_second_moment_gaussian():
 # ------------------------------------------------------ App. B sparse matrices
 @pytest.mark.parametrize("n,p,seed", [(6, 0.2, 1), (8, 0.1, 2), (12, 0.1, 3), (16, 0.05, 4), (18, 0.15, 5)])
 def test_sparse_vs_glynn(n, p, seed):
-    A = O.sparse_matrix(n, p, seed)
+    A = W.sparse_matrix(n, p, seed)
     block = O.greedy_partition(A)
     assert O.partition_count(block) <= 1 << n
     r = O.per_sparse(A, block)
@@ -343,7 +343,7 @@ def test_sparse_vs_glynn(n, p, seed):
 
 
 def test_sparse_partition_properties():
-    A = O.sparse_matrix(30, 0.05, 9)
+    A = W.sparse_matrix(30, 0.05, 9)
     rng = np.random.default_rng(0)
     for block in (O.greedy_partition(A), O.greedy_partition(A, rng)):
         nb = max(block) + 1
