@@ -61,7 +61,8 @@ def test_closed_forms():
         assert abs(gpu_rep(np.ones((n, 1)), [n]) - math.factorial(n)) <= tol(n, math.factorial(n), asum)
     c = W.complex_gaussian(10, 4)[:, :1]
     ref = math.factorial(10) * np.prod(c[:, 0])
-    assert abs(gpu_rep(c, [10]) - ref) <= 1e-13 * abs(ref)
+    asum = O.per_repeated(c, [10])[2]
+    assert abs(gpu_rep(c, [10]) - ref) <= tol(10, ref, asum)
 
 
 def test_errors_and_host_buffers():
