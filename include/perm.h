@@ -111,11 +111,15 @@ int perm_c128_noalloc(const double* A, int n, double* out, void* stream);
 int perm_c128_f32p(const double* A, int n, double* out, void* stream);
 int perm_f64_f32p(const double* A, int n, double* out, void* stream);
 
-/* ---- Repeated columns: the weighted Ryser formula, Eq.(ryser2) of Sec. 2.A ----
- *   per(A) = (-1)^n sum_{0<=f_k<=m_k} (-1)^{sum f} (prod_k binom(m_k, f_k)) prod_i sum_k f_k cbar_k(i)
- * for the n x n matrix A whose R distinct columns cbar_1..cbar_R appear m_k
+/* ---- Repeated columns: the multiplicity classes of Eq.(ryser2), Sec. 2.A ----
+ * For the n x n matrix A whose R distinct columns cbar_1..cbar_R appear m_k
  * times each (sum_k m_k = n; Boson-sampling outputs with several photons in
- * one mode give such matrices).  prod_k (m_k + 1) terms instead of 2^(n-1).
+ * one mode give such matrices), the terms of the sum are grouped by
+ * multiplicity as in Eq.(ryser2), but in Glynn's halved form (the form of
+ * App. A), which is far better conditioned than the un-halved one:
+ *   per(A) = 2^(1-n) sum_g (-1)^{sum g} C(m_1 - 1, g_1) prod_{k>1} C(m_k, g_k)
+ *            prod_i sum_k (m_k - 2 g_k) cbar_k(i),
+ * m_1 prod_{k>1} (m_k + 1) terms instead of 2^(n-1).
  * C: n x R complex matrix of the distinct columns, row-major interleaved
  *    (C[2*(i*R+k)] = Re cbar_k(i)); device or host memory.
  * mult: HOST array of R multiplicities >= 1 summing to n; 1 <= R <= n <= 64;

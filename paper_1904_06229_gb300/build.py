@@ -34,6 +34,7 @@ SOURCES = [
     "walk_fx_r64_f64.cu",
     "walk_fx_c128_f32.cu",
     "walk_fx_r64_f32.cu",
+    "walk_df_c128.cu",
     "glynn_mod.cu",
     "ryser2.cu",
     "band.cu",

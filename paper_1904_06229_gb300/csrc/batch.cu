@@ -166,7 +166,7 @@ int batch_resident_blocks_t() {
 }
 
 int batch_resident_blocks_rows(RowMode rows) {
-  return rows == kRowsFixed ? batch_resident_blocks_t<kRowsFixed>() : batch_resident_blocks_t<kRowsF64>();
+  return rows == kRowsF64 ? batch_resident_blocks_t<kRowsF64>() : batch_resident_blocks_t<kRowsFixed>();
 }
 
 int batch_resident_blocks() { return batch_resident_blocks_rows(rows_from_env()); }
@@ -258,7 +258,7 @@ struct Tune {
 Tune g_tune_tab[2][64];  // [row mode][device]
 
 // Tuning table of the row arithmetic currently selected (PERM_ROWS).
-Tune& tune_of(int dev) { return g_tune_tab[rows_from_env() == kRowsFixed ? 1 : 0][dev]; }
+Tune& tune_of(int dev) { return g_tune_tab[rows_from_env() == kRowsF64 ? 0 : 1][dev]; }
 
 int default_L(int n) {
   // about 16 n codes per lane keeps the O(n^2) seed near 2% of the walk
@@ -343,7 +343,7 @@ int enqueue_batch(const double* const* ptrs, const BatchItem* d_items, int nitem
   if (grid < 1) return PERM_ECUDA;
   cudaError_t e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return status_of_b(e);
-  if (rows == kRowsFixed)
+  if (rows != kRowsF64)
     k_batch<kRowsFixed><<<grid, kBatchThreads, kBatchSmem, s>>>(ptrs, d_items, nitems, d_partials, d_ticket, status);
   else
     k_batch<kRowsF64><<<grid, kBatchThreads, kBatchSmem, s>>>(ptrs, d_items, nitems, d_partials, d_ticket, status);

@@ -42,17 +42,25 @@ struct FxShape {
 };
 
 // Double with value v * 2^(eb - 1086) (eb = 1086 - scale exponent), from the
-// bits of v only: |v| normalised by its leading-zero count, rounded to 53
-// significant bits (half-way cases away from zero), exponent field from the
-// leading-zero count.  0 for v == 0 and for results below the normal range.
+// bits of v only: |v| normalised by its leading-zero count, 52 fraction bits
+// kept, exponent field from the leading-zero count.  RN = false truncates
+// (the Gray walks: a truncation bias scales every term alike and does not
+// meet the sum's cancellation); RN = true rounds to nearest (half-way cases
+// away from zero; used by the un-halved sums, whose terms are all large).
+// 0 for v == 0 and for results below the normal range.
+template <bool RN = false>
 __device__ __forceinline__ double fx_to_double(long long v, int eb) {
   const unsigned long long s = (unsigned long long)(v >> 63);
   const unsigned long long m = ((unsigned long long)v ^ s) - s;
   const int lz = __clzll((long long)m);
-  const unsigned long long mn = m << (lz & 63);
-  const unsigned long long rn = mn + 0x400ull;  // + half a unit of the 53rd bit
-  const int up = rn < mn ? 1 : 0;               // rounding carried past bit 63
-  const uint32_t hi = (uint32_t)(rn >> 32), lo = (uint32_t)rn;
+  unsigned long long mn = m << (lz & 63);
+  int up = 0;
+  if constexpr (RN) {
+    const unsigned long long rn = mn + 0x400ull;  // + half a unit of the 53rd bit
+    up = rn < mn ? 1 : 0;                         // rounding carried past bit 63
+    mn = rn;
+  }
+  const uint32_t hi = (uint32_t)(mn >> 32), lo = (uint32_t)mn;
   const int be = eb - lz + up;  // biased exponent of the result
   const uint32_t dhi = ((uint32_t)s & 0x80000000u) | ((uint32_t)be << 20) | ((hi >> 11) & 0xFFFFFu);
   const uint32_t dlo = (hi << 21) | (lo >> 11);
@@ -72,24 +80,24 @@ __device__ __forceinline__ float fx_to_f32(long long v, int lzref) {
   return (m == 0 || fexp <= 0) ? 0.0f : __int_as_float((int)bits);
 }
 
-template <int N, bool CPLX, int MODE>
+template <int N, bool CPLX, int MODE, bool RN = false>
 struct FxProduct;
 
 // FP64 product of w_i = v_i 2^(eb_i - 1086), two interleaved chains.
-template <int N>
-struct FxProduct<N, true, kProdF64> {
+template <int N, bool RN>
+struct FxProduct<N, true, kProdF64, RN> {
   static __device__ __forceinline__ void eval(const long long (&vr)[N], const long long (&vi)[N], const int* sEb,
                                               double& pr, double& pi, double z) {
-    double ar = fx_to_double(vr[0], sEb[0]), ai = fx_to_double(vi[0], sEb[0]);
+    double ar = fx_to_double<RN>(vr[0], sEb[0]), ai = fx_to_double<RN>(vi[0], sEb[0]);
     if constexpr (N == 1) {
       pr = ar;
       pi = ai;
     } else {
-      double br = fx_to_double(vr[1], sEb[1]), bi = fx_to_double(vi[1], sEb[1]);
+      double br = fx_to_double<RN>(vr[1], sEb[1]), bi = fx_to_double<RN>(vi[1], sEb[1]);
 #pragma unroll
       for (int i = 2; i < N; ++i) {
         const int eb = sEb[i];
-        const double cr = fx_to_double(vr[i], eb), ci = fx_to_double(vi[i], eb);
+        const double cr = fx_to_double<RN>(vr[i], eb), ci = fx_to_double<RN>(vi[i], eb);
         if (i & 1)
           cmul(br, bi, cr, ci, z);
         else
@@ -102,17 +110,17 @@ struct FxProduct<N, true, kProdF64> {
   }
 };
 
-template <int N>
-struct FxProduct<N, false, kProdF64> {
+template <int N, bool RN>
+struct FxProduct<N, false, kProdF64, RN> {
   static __device__ __forceinline__ void eval(const long long (&v)[N], const int* sEb, double& p, double z) {
-    double a = fx_to_double(v[0], sEb[0]);
+    double a = fx_to_double<RN>(v[0], sEb[0]);
     if constexpr (N == 1) {
       p = a;
     } else {
-      double b = fx_to_double(v[1], sEb[1]);
+      double b = fx_to_double<RN>(v[1], sEb[1]);
 #pragma unroll
       for (int i = 2; i < N; ++i) {
-        const double c = fx_to_double(v[i], sEb[i]);
+        const double c = fx_to_double<RN>(v[i], sEb[i]);
         if (i & 1)
           b = fma(b, c, z);
         else
@@ -124,8 +132,8 @@ struct FxProduct<N, false, kProdF64> {
 };
 
 // FP32 significands straight from the integers; exponents add in integers.
-template <int N>
-struct FxProduct<N, true, kProdF32> {
+template <int N, bool RN>
+struct FxProduct<N, true, kProdF32, RN> {
   static __device__ __forceinline__ void eval(const long long (&vr)[N], const long long (&vi)[N], const int* sEb,
                                               double& pr, double& pi, double) {
     float ar = 1.f, ai = 0.f, br = 1.f, bi = 0.f;
@@ -156,8 +164,8 @@ struct FxProduct<N, true, kProdF32> {
   }
 };
 
-template <int N>
-struct FxProduct<N, false, kProdF32> {
+template <int N, bool RN>
+struct FxProduct<N, false, kProdF32, RN> {
   static __device__ __forceinline__ void eval(const long long (&v)[N], const int* sEb, double& p, double) {
     float a = 1.f, b = 1.f;
     int E = 0;

@@ -47,10 +47,13 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const double* __restri
       tr = dd_add(tr, sRed[2 * w]);
       ti = dd_add(ti, sRed[2 * w + 1]);
     }
-    if (mode == 0 || mode == 2) {
+    if (mode == 0 || mode == 2 || mode == 3) {
       // mode 0: per = 2 (-1)^(n-1) * sum (halved Glynn form)
-      // mode 2: per = (-1)^n * sum (Eq. ryser2); scaling by +-2 or +-1 is exact
-      const double s = mode == 0 ? (((n - 1) & 1) ? -2.0 : 2.0) : ((n & 1) ? -1.0 : 1.0);
+      // mode 2: per = (-1)^n * sum (Ryser's un-halved form)
+      // mode 3: per = 2^(1-n) * sum (Glynn's form with column multiplicities)
+      const double s = mode == 0 ? (((n - 1) & 1) ? -2.0 : 2.0)
+                       : mode == 2 ? ((n & 1) ? -1.0 : 1.0)
+                                   : __hiloint2double((1023 + 1 - n) << 20, 0);  // exact power of two
       out[0] = s * __dadd_rn(tr.hi, tr.lo);
       if (cplx) out[1] = s * __dadd_rn(ti.hi, ti.lo);
     } else {
@@ -92,10 +95,14 @@ int device_status_word(int dev, int** out) {
 
 RowMode rows_from_env() {
   const char* e = std::getenv("PERM_ROWS");
-  return (e && std::strcmp(e, "fp64") == 0) ? kRowsF64 : kRowsFixed;
+  if (e && std::strcmp(e, "fp64") == 0) return kRowsF64;
+  if (e && std::strcmp(e, "df") == 0) return kRowsDf;
+  return kRowsFixed;
 }
 
 int walk_resident_blocks(int n, bool cplx, ProductMode mode, RowMode rows) {
+  if (rows == kRowsDf && cplx && mode == kProdF64) return walk_blocks_df_c128(n);
+  if (rows == kRowsDf) rows = kRowsFixed;
   if (rows == kRowsFixed) {
     if (mode == kProdF64) {
       if (cplx) return n <= 32 ? walk_blocks_fx_c128_f64_lo(n) : walk_blocks_fx_c128_f64_hi(n);
@@ -111,6 +118,8 @@ int walk_resident_blocks(int n, bool cplx, ProductMode mode, RowMode rows) {
 }
 
 cudaError_t walk_launch(bool cplx, ProductMode mode, const WalkArgs& a, RowMode rows) {
+  if (rows == kRowsDf && cplx && mode == kProdF64) return walk_launch_df_c128(a);
+  if (rows == kRowsDf) rows = kRowsFixed;
   if (rows == kRowsFixed) {
     if (mode == kProdF64) {
       if (cplx) return a.n <= 32 ? walk_launch_fx_c128_f64_lo(a) : walk_launch_fx_c128_f64_hi(a);

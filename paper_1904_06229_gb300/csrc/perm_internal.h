@@ -23,10 +23,12 @@ enum ProductMode : int {
 enum RowMode : int {
   kRowsF64 = 0,    // FP64 row sums, DFMA updates, periodic re-seed (glynn_walk.cuh)
   kRowsFixed = 1,  // exact int64 fixed-point row sums, integer updates (glynn_walk_fx.cuh)
+  kRowsDf = 2,     // double-float row sums and products on the FP32 pipe (glynn_walk_df.cuh);
+                   // complex FP64-product walks only, the others use kRowsFixed
 };
 
 // Row arithmetic for the floating-point entry points: PERM_ROWS=fp64 selects
-// kRowsF64, anything else (default) kRowsFixed.
+// kRowsF64, PERM_ROWS=df kRowsDf, anything else (default) kRowsFixed.
 RowMode rows_from_env();
 
 struct WalkArgs {
@@ -53,6 +55,8 @@ cudaError_t walk_launch_c128_f64_hi(const WalkArgs& a);   // n in 33..64
 cudaError_t walk_launch_r64_f64(const WalkArgs& a);       // n in 1..64
 cudaError_t walk_launch_c128_f32(const WalkArgs& a);      // n in 1..64
 cudaError_t walk_launch_r64_f32(const WalkArgs& a);       // n in 1..64
+cudaError_t walk_launch_df_c128(const WalkArgs& a);  // double-float rows and products
+int walk_blocks_df_c128(int n);
 cudaError_t walk_launch_fx_c128_f64_lo(const WalkArgs& a);  // fixed-point rows
 cudaError_t walk_launch_fx_c128_f64_hi(const WalkArgs& a);
 cudaError_t walk_launch_fx_r64_f64(const WalkArgs& a);
@@ -72,7 +76,8 @@ int walk_blocks_r64_f32(int n);
 // Fixed-order reduction of per-block dd partials.
 //   mode 0: out = 2 (-1)^(n-1) * sum, rounded to double(s)  (1 or 2 doubles)
 //   mode 1: out = sum as dd                                    (2 or 4 doubles)
-//   mode 2: out = (-1)^n * sum, rounded to double(s)            (Eq. ryser2)
+//   mode 2: out = (-1)^n * sum, rounded to double(s)            (Ryser's un-halved form)
+//   mode 3: out = 2^(1-n) * sum, rounded to double(s)           (Glynn's form with multiplicities)
 cudaError_t finalize_launch(const double* partials, int nparts, bool cplx, int n, int mode, double* out,
                             cudaStream_t stream);
 

@@ -1,22 +1,31 @@
-// Permanents of matrices with repeated columns by the weighted form of
-// Ryser's formula, Eq.(ryser2) of Sec. 2.A:
+// Permanents of matrices with repeated columns: the multiplicity classes of
+// Eq.(ryser2), Sec. 2.A.
 //
-//   per(A) = (-1)^n sum_{0 <= f_k <= m_k} (-1)^{sum_k f_k} (prod_k binom(m_k, f_k))
-//            prod_i sum_k f_k cbar_k(i)
+// A has R distinct columns cbar_k, column k repeated m_k times.  Eq.(ryser2)
+// groups Ryser's subsets by how many copies of each distinct column they
+// hold, so the sum has prod_k (m_k + 1) terms instead of 2^n.  The kernel
+// groups the terms of Glynn's halved form the same way -- the form App. A
+// uses for general matrices -- because it is far better conditioned (on
+// Haar submatrices with 8 doubled columns the un-halved sum's condition
+// number is about 1.7e5, the halved one's about 1e2):
 //
-// where A has R distinct columns cbar_k, column k repeated m_k times.  The
-// sum has prod_k (m_k + 1) terms instead of 2^(n-1).
+//   per(A) = 2^(1-n) sum_{g} (-1)^{sum g} C(m_0 - 1, g_0) prod_{k>=1} C(m_k, g_k)
+//            prod_i sum_k (m_k - 2 g_k) cbar_k(i),
+//
+// g_k = how many of column k's copies carry the sign -1 (one copy of column 0
+// is fixed to +1, so 0 <= g_0 <= m_0 - 1 and 0 <= g_k <= m_k otherwise):
+// m_0 prod_{k>=1} (m_k + 1) terms.  Tests compare it with the oracle's literal
+// evaluation of Eq.(ryser2) and with the Gray walk of the expanded matrix.
 //
 // Walk: each thread takes a contiguous range of the mixed-radix counting
-// index of f (digit 0 fastest) and keeps the row sums s_i = sum_k f_k cbar_k(i)
-// as exact int64 fixed point (per-row power-of-two scale, as in the
-// fixed-point Gray walk): stepping digit 0 adds C_0, a carry subtracts
-// m_k C_k and adds C_{k+1}; none of this rounds, so nothing drifts however
-// often carries happen.  The weight is exact table values: binom(m_0, f_0)
-// times the product over the other digits, which changes only on a carry.
-// The signed weight multiplies the FP64 product, and every term is added
-// into double-double accumulators (Eq. ryser2 cancels much more than the
-// halved Gray sum does).
+// index of g (digit 0 fastest) and keeps the row sums
+// s_i = sum_k (m_k - 2 g_k) cbar_k(i) as exact int64 fixed point (per-row
+// power-of-two scale, as in the fixed-point Gray walk): stepping digit k
+// subtracts 2 C_k, a carry adds 2 gmax_k C_k back; none of this rounds.  The
+// weight is exact table values: C(gmax_0, g_0) times the product over the
+// other digits, which changes only on a carry.  The signed weight multiplies
+// the FP64 product; terms are summed like the Gray walk's (FP64 run sums
+// folded into double-double).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -34,13 +43,14 @@ constexpr int kR2MaxR = PERM_NMAX;
 struct R2Params {
   int R;
   int mult[kR2MaxR];
-  int bin_off[kR2MaxR];  // offset of column k's binomial row in the table
+  int gmax[kR2MaxR];     // m_0 - 1 for column 0, m_k otherwise
+  int bin_off[kR2MaxR];  // offset of row C(gmax_k, .) in the binomial table
 };
 
 template <int N>
 struct R2Shape {
-  // +C_k and m_k C_k (int64 pairs, R columns), binomials (<= 2N + R doubles),
-  // row exponent biases and scales, reduction slots
+  // 2 C_k (step) and 2 gmax_k C_k (carry) as int64 pairs, R columns; the
+  // binomial rows; row exponent biases and scales; reduction slots
   static size_t smem(int R, int nbin) {
     return (size_t)2 * R * N * sizeof(longlong2) + (size_t)nbin * sizeof(double) + 2 * N * sizeof(int) +
            8 * sizeof(dd) + 16;
@@ -53,9 +63,9 @@ __global__ void __launch_bounds__(kWalkThreads) k_ryser2(const double* __restric
                                                          int* __restrict__ status) {
   extern __shared__ __align__(16) long long r2sm[];
   const int R = prm.R;
-  longlong2* sCp = reinterpret_cast<longlong2*>(r2sm);  // [k * N + i] = C_ik
-  longlong2* sCm = sCp + R * N;                          // [k * N + i] = m_k C_ik
-  double* sBin = reinterpret_cast<double*>(sCm + R * N);
+  longlong2* sStep = reinterpret_cast<longlong2*>(r2sm);  // [k * N + i] = 2 C_ik
+  longlong2* sReset = sStep + R * N;                       // [k * N + i] = 2 gmax_k C_ik
+  double* sBin = reinterpret_cast<double*>(sReset + R * N);
   int* sEb = reinterpret_cast<int*>(sBin + nbin);
   int* sF = sEb + N;
   dd* sRed = reinterpret_cast<dd*>(r2sm);  // reused after the walk
@@ -89,17 +99,17 @@ __global__ void __launch_bounds__(kWalkThreads) k_ryser2(const double* __restric
       const double2 v = C[idx];
       const int F = sF[i];
       const long long qr = __double2ll_rn(scalbn(v.x, F)), qi = __double2ll_rn(scalbn(v.y, F));
-      sCp[k * N + i] = make_longlong2(qr, qi);
-      sCm[k * N + i] = make_longlong2((long long)prm.mult[k] * qr, (long long)prm.mult[k] * qi);
+      sStep[k * N + i] = make_longlong2(2 * qr, 2 * qi);
+      sReset[k * N + i] = make_longlong2(2 * (long long)prm.gmax[k] * qr, 2 * (long long)prm.gmax[k] * qi);
     }
     for (int k = threadIdx.x; k < R; k += blockDim.x) {
-      // binom(m, f) for f = 0..m by the multiplicative recurrence (exact while < 2^53)
-      const int m = prm.mult[k];
+      // C(gm, g) for g = 0..gm by the multiplicative recurrence (exact while < 2^53)
+      const int gm = prm.gmax[k];
       double b = 1.0;
       sBin[prm.bin_off[k]] = 1.0;
-      for (int f = 1; f <= m; ++f) {
-        b = b * (double)(m - f + 1) / (double)f;
-        sBin[prm.bin_off[k] + f] = b;
+      for (int g = 1; g <= gm; ++g) {
+        b = b * (double)(gm - g + 1) / (double)g;
+        sBin[prm.bin_off[k] + g] = b;
       }
     }
   }
@@ -113,13 +123,13 @@ __global__ void __launch_bounds__(kWalkThreads) k_ryser2(const double* __restric
   } else if (r < end) {
     const double z = sBin[0] * 0.0;  // register zero for the product FMAs
     // ---- seed: digits of r, row sums from scratch, weight of the upper digits
-    int f[kR2MaxR];
+    int g[kR2MaxR];
     {
       uint64_t q = r;
 #pragma unroll 1
       for (int k = 0; k < R; ++k) {
-        const uint64_t rad = (uint64_t)prm.mult[k] + 1;
-        f[k] = (int)(q % rad);
+        const uint64_t rad = (uint64_t)prm.gmax[k] + 1;
+        g[k] = (int)(q % rad);
         q /= rad;
       }
     }
@@ -131,9 +141,11 @@ __global__ void __launch_bounds__(kWalkThreads) k_ryser2(const double* __restric
         long long sr = 0, si = 0;
 #pragma unroll 1
         for (int k = 0; k < R; ++k) {
-          const longlong2 c = sCp[k * N + i];
-          sr += (long long)f[k] * c.x;
-          si += (long long)f[k] * c.y;
+          // (m_k - 2 g_k) C_ik = (m_k - 2 g_k) / 2 * (2 C_ik), exact
+          const longlong2 c = sStep[k * N + i];
+          const long long f = prm.mult[k] - 2 * g[k];
+          sr += f * (c.x / 2);
+          si += f * (c.y / 2);
         }
         seed[i] = make_longlong2(sr, si);
       }
@@ -143,73 +155,74 @@ __global__ void __launch_bounds__(kWalkThreads) k_ryser2(const double* __restric
         vi[i] = seed[i].y;
       }
     }
-    const int m0 = prm.mult[0];
+    const int gmax0 = prm.gmax[0];
     const double* bin0 = sBin;  // bin_off[0] == 0
-    int f0 = f[0];
+    int g0 = g[0];
     double wrest = 1.0;
-    int par = f0;
+    int par = g0;
 #pragma unroll 1
-    for (int k = 1; k < R; ++k) wrest *= sBin[prm.bin_off[k] + f[k]], par += f[k];
+    for (int k = 1; k < R; ++k) wrest *= sBin[prm.bin_off[k] + g[k]], par += g[k];
     uint32_t odd = (uint32_t)(par & 1);
-    {
-      // Eq.(ryser2) sums terms of both signs and very different sizes (its
-      // condition number grows much faster than the halved Gray sum's), so
-      // every term goes straight into the double-double accumulators.
-      for (; r < end; ++r) {
+    while (r < end) {
+      const uint64_t run_end = min(end, r + kRun);
+      double sr = 0.0, si = 0.0;
+      for (; r < run_end; ++r) {
         double pr, pi;
         FxProduct<N, true, kProdF64>::eval(vr, vi, sEb, pr, pi, z);
-        const double sw = flip_sign(fma(wrest, bin0[f0], z), odd);  // (-1)^{sum f} prod binom
-        accr = dd_add_d(accr, fma(sw, pr, z));
-        acci = dd_add_d(acci, fma(sw, pi, z));
+        const double sw = flip_sign(fma(wrest, bin0[g0], z), odd);  // (-1)^{sum g} prod binom
+        sr = fma(sw, pr, sr);
+        si = fma(sw, pi, si);
         if (r + 1 >= end) continue;  // no step past this thread's range
-        if (f0 < m0) {
-          ++f0;
+        if (g0 < gmax0) {
+          ++g0;
           odd ^= 1u;
 #pragma unroll
           for (int i = 0; i < N; ++i) {
-            const longlong2 c = sCp[i];
-            vr[i] += c.x;
-            vi[i] += c.y;
+            const longlong2 c = sStep[i];
+            vr[i] -= c.x;
+            vi[i] -= c.y;
           }
         } else {
           // carry: digit 0 back to 0, then every digit at its maximum back to
           // 0, then the next digit up by one
 #pragma unroll
           for (int i = 0; i < N; ++i) {
-            const longlong2 c = sCm[i];
-            vr[i] -= c.x;
-            vi[i] -= c.y;
+            const longlong2 c = sReset[i];
+            vr[i] += c.x;
+            vi[i] += c.y;
           }
-          f0 = 0;
+          g0 = 0;
           int k = 1;
-          while (k < R && f[k] == prm.mult[k]) {
-            const longlong2* cm = sCm + k * N;
+          while (k < R && g[k] == prm.gmax[k]) {
+            const longlong2* cr = sReset + k * N;
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-              const longlong2 c = cm[i];
-              vr[i] -= c.x;
-              vi[i] -= c.y;
+              const longlong2 c = cr[i];
+              vr[i] += c.x;
+              vi[i] += c.y;
             }
-            f[k] = 0;
+            g[k] = 0;
             ++k;
           }
           if (k < R) {
-            ++f[k];
-            const longlong2* cp = sCp + k * N;
+            ++g[k];
+            const longlong2* cs = sStep + k * N;
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-              const longlong2 c = cp[i];
-              vr[i] += c.x;
-              vi[i] += c.y;
+              const longlong2 c = cs[i];
+              vr[i] -= c.x;
+              vi[i] -= c.y;
             }
           }
           wrest = 1.0;
           par = 0;
 #pragma unroll 1
-          for (int kk = 1; kk < R; ++kk) wrest *= sBin[prm.bin_off[kk] + f[kk]], par += f[kk];
+          for (int kk = 1; kk < R; ++kk) wrest *= sBin[prm.bin_off[kk] + g[kk]], par += g[kk];
           odd = (uint32_t)(par & 1);
         }
       }
+      accr = dd_add_d(accr, sr);
+      acci = dd_add_d(acci, si);
     }
   }
   __syncthreads();
@@ -276,11 +289,12 @@ extern "C" int perm_c128_repeated(const double* C, const int* mult, int R, int n
   for (int k = 0; k < R; ++k) {
     if (mult[k] < 1) return PERM_EINVAL;
     p.mult[k] = mult[k];
+    p.gmax[k] = k == 0 ? mult[k] - 1 : mult[k];
     p.bin_off[k] = nbin;
-    nbin += mult[k] + 1;
+    nbin += p.gmax[k] + 1;
     sum += mult[k];
-    if (total > (1ull << 62) / (uint64_t)(mult[k] + 1)) return PERM_EINVAL;  // more than 2^62 terms
-    total *= (uint64_t)(mult[k] + 1);
+    if (total > (1ull << 62) / (uint64_t)(p.gmax[k] + 1)) return PERM_EINVAL;  // more than 2^62 terms
+    total *= (uint64_t)(p.gmax[k] + 1);
   }
   if (sum != n) return PERM_EINVAL;
   int ndev = 0, dev = 0;
@@ -321,7 +335,7 @@ extern "C" int perm_c128_repeated(const double* C, const int* mult, int R, int n
   double* partials = (double*)(base + szC);
   double* dOut = o_dev ? out : (double*)(base + szC + szP);
   if (e == cudaSuccess) e = r2_dispatch<1, PERM_NMAX>(n, dC, p, nbin, total, partials, blocks, status, s, nullptr);
-  if (e == cudaSuccess) e = finalize_launch(partials, blocks, true, n, 2, dOut, s);
+  if (e == cudaSuccess) e = finalize_launch(partials, blocks, true, n, 3, dOut, s);
   if (e == cudaSuccess && !o_dev) e = cudaMemcpyAsync(out, dOut, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
   cudaFreeAsync(base, s);
   return e == cudaSuccess ? PERM_OK : PERM_ECUDA;

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_sparse(const double* __restric
     const int t0 = prm.size[0];
     for (; r < end; ++r) {
       double pr, pi;
-      FxProduct<N, true, kProdF64>::eval(vr, vi, sEb, pr, pi, z);
+      FxProduct<N, true, kProdF64, true>::eval(vr, vi, sEb, pr, pi, z);
       accr = dd_add_d(accr, flip_sign(pr, odd));  // (-1)^|J| prod_i s_i
       acci = dd_add_d(acci, flip_sign(pi, odd));
       if (r + 1 >= end) continue;
