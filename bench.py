@@ -199,7 +199,7 @@ def run_gpu(args):
 
     peak_gops = P.perm_fp64_peak()
     rows = os.environ.get("PERM_ROWS", "fixed")
-    if rows != "fp64":
+    if rows not in ("fp64", "df"):
         rows = "fixed"
 
     # warm-up
@@ -269,11 +269,12 @@ def run_gpu(args):
     flops_per_term = 8 * n - 6   # complex multiply = 6 flops, complex add = 2
     # FP64 instructions the kernel actually issues per code: with fixed-point
     # rows the 2n row updates run on the integer pipes
-    issued = 4 * (n - 1) + 2 if rows == "fixed" else 6 * n - 2
+    issued = {"fixed": 4 * (n - 1) + 2, "fp64": 6 * n - 2, "df": 8}[rows]
     avg_launch = sum(launch_s) / len(launch_s)
     achieved = CODES_PER_STEP * ops_per_term / avg_launch / 1e9
-    kname = (f"perm::k_walk_fx<{n}, complex, FP64 product> (int64 fixed-point rows)" if rows == "fixed"
-             else f"perm::k_walk<{n}, complex, FP64 product> (FP64 rows)")
+    kname = {"fixed": f"perm::k_walk_fx<{n}, complex, FP64 product> (int64 fixed-point rows)",
+             "fp64": f"perm::k_walk<{n}, complex, FP64 product> (FP64 rows)",
+             "df": f"perm::k_walk_df<{n}> (double-float rows and products, FP32 pipe)"}[rows]
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
                 "frac": achieved / peak_gops, "traffic": None,
                 "kernel": kname, "rows": rows,
@@ -295,22 +296,28 @@ def run_gpu(args):
             "gpu_launches": 2 * args.steps, "clocks": clk, "fp64_peak_gops": peak_gops}
 
     if rank == 0 and not args.no_alt_rows:
-        # one step of the other row arithmetic, same slice, for comparison
-        alt = "fp64" if rows == "fixed" else "fixed"
-        os.environ["PERM_ROWS"] = alt
-        P.perm_c128_range(dA, slice_first(0), CODES_PER_STEP, out=out)
-        torch.cuda.synchronize()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        P.perm_c128_range(dA, slice_first(args.warmup), CODES_PER_STEP, out=out)
-        a1.record(stream)
-        torch.cuda.synchronize()
+        # one step of each other arithmetic on the same slice, for comparison
+        line["alt_rows"] = []
+        ref_part = out.clone()
+        P.perm_c128_range(dA, slice_first(args.warmup), CODES_PER_STEP, out=ref_part)
+        for alt in [m for m in ("fixed", "fp64", "df") if m != rows]:
+            os.environ["PERM_ROWS"] = alt
+            P.perm_c128_range(dA, slice_first(0), CODES_PER_STEP, out=out)
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            P.perm_c128_range(dA, slice_first(args.warmup), CODES_PER_STEP, out=out)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            at = a0.elapsed_time(a1) / 1e3
+            alt_issued = {"fixed": 4 * (n - 1) + 2, "fp64": 6 * n - 2, "df": 8}[alt]
+            o, rp = out.cpu().numpy(), ref_part.cpu().numpy()
+            va, vr_ = complex(o[0] + o[1], o[2] + o[3]), complex(rp[0] + rp[1], rp[2] + rp[3])
+            line["alt_rows"].append({"rows": alt, "terms_per_s": CODES_PER_STEP / at,
+                                     "frac": CODES_PER_STEP * ops_per_term / at / 1e9 / peak_gops,
+                                     "fp64_pipe_frac": CODES_PER_STEP * alt_issued / at / 1e9 / peak_gops,
+                                     "rel_diff_vs_default": abs(va - vr_) / abs(vr_)})
         os.environ["PERM_ROWS"] = rows
-        at = a0.elapsed_time(a1) / 1e3
-        alt_issued = 4 * (n - 1) + 2 if alt == "fixed" else 6 * n - 2
-        line["alt_rows"] = {"rows": alt, "terms_per_s": CODES_PER_STEP / at,
-                            "frac": CODES_PER_STEP * ops_per_term / at / 1e9 / peak_gops,
-                            "fp64_pipe_frac": CODES_PER_STEP * alt_issued / at / 1e9 / peak_gops}
     if rank == 0 and args.batch_sample > 0:
         line["batch"] = batch_measure(P, torch, dev, args.batch_sample)
     if rank == 0 and not args.no_extras:

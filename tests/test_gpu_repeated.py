@@ -52,18 +52,25 @@ def test_vs_gray_walk_of_expanded(mult):
     full = P.perm_c128(torch.from_numpy(A).cuda()).cpu().numpy()
     ref = complex(full[0], full[1])
     got = gpu_rep(Cb, mult)
-    assert abs(got - ref) <= REL * abs(ref), (got, ref)
+    # matrices with repeated columns have large condition numbers (repeated
+    # columns make the permanent small against its terms); both GPU sums
+    # carry up to ~kappa n u, bounded here by the oracle's sum|t| of Eq.(ryser2)
+    asum = O.per_repeated(Cb, mult)[2]
+    assert abs(got - ref) <= tol(n, ref, asum), (got, ref, float(asum))
 
 
 def test_boson_sampling_collisions_n30():
     """15 modes with two photons each on a Haar S(900, 30) submatrix: the
-    halved multiplicity form against the expanded matrix's Gray walk."""
+    halved multiplicity form against the expanded matrix's Gray walk.  Merging
+    equal terms leaves the condition number unchanged, about 4.6e5 for this
+    input (sum of term magnitudes over |per|), so either result may be off by
+    up to ~kappa n u = 1.5e-9; the bound allows 1e-8."""
     Cb = W.haar_submatrix(30, 900, 30)[:, :15]
     A = W.expand_columns(Cb, [2] * 15)
     full = P.perm_c128(torch.from_numpy(A).cuda()).cpu().numpy()
     ref = complex(full[0], full[1])
     got = gpu_rep(Cb, [2] * 15)
-    assert abs(got - ref) <= REL * abs(ref), (got, ref)
+    assert abs(got - ref) <= 1e-8 * abs(ref), (got, ref)
 
 
 def test_closed_forms():
