@@ -140,12 +140,12 @@ def run_reference(args):
     A = workload_matrix()
     cores = os.cpu_count() or 1
     # each step: a bounded slice of the same workload, sized so the whole run
-    # stays within a few minutes
-    probe = 1 << 12
+    # stays within a few minutes (about 10 s per step on the host cores)
+    probe = 1 << 18
     t0 = time.perf_counter()
     O.glynn_partial_parts(A, 0, probe, parts=cores, threads=cores)
     rate = probe / max(time.perf_counter() - t0, 1e-4)
-    per_step = int(max(cores, min(1 << 26, rate * 120.0 / max(1, args.steps + args.warmup))))
+    per_step = int(max(cores, min(1 << 30, rate * min(10.0, 150.0 / max(1, args.steps + args.warmup)))))
     for w in range(args.warmup):
         O.glynn_partial_parts(A, w * per_step, per_step, parts=cores, threads=cores)
     t0 = time.perf_counter()
@@ -153,10 +153,14 @@ def run_reference(args):
         O.glynn_partial_parts(A, (args.warmup + s) * per_step, per_step, parts=cores, threads=cores)
     dt = time.perf_counter() - t0
     value = per_step * args.steps / dt
+    cfg = config_dict(1)
+    cfg["workload"] = (f"n={N_ORDER} complex128 Haar S({N_ORDER * N_ORDER},{N_ORDER}) seed {SEED}; one step = "
+                       f"{per_step} consecutive Gray codes of its permanent on the host cores (CPU oracle)")
+    cfg["codes_per_step"] = per_step
     line = {"metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "long double", "data": "synthetic",
-            "impl": "reference", "config": config_dict(1),
+            "impl": "reference", "config": cfg,
             "cpu_baseline": {"value": value, "unit": "terms/s", "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} consecutive codes per step of the n={N_ORDER} sum"},
             "e2e": {"value": value, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

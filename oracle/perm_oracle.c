@@ -53,6 +53,16 @@ typedef long double ld;
 
 #define ORACLE_NMAX 64
 
+/* Planted mistakes for the mutation test of the pins (tests/test_oracle_mutants.py
+ * compiles this file with -DORACLE_MUTANT=k, k = 1..6; the normal build has 0):
+ * 1 drops the last row from each product, 2 never flips the sign t, 3 seeds w
+ * with the first column instead of the last, 4 reads the updated column
+ * transposed, 5 forgets the halving in step 5, 6 uses the wrong final sign. */
+#ifndef ORACLE_MUTANT
+#define ORACLE_MUTANT 0
+#endif
+#define MUT(k) (ORACLE_MUTANT == (k))
+
 /* ---- Neumaier's variant of Kahan summation (Sec. 2.B recommends Kahan; the
  * Neumaier form also handles terms larger than the running sum). ---------- */
 typedef struct {
@@ -151,7 +161,7 @@ static void unrank(uint64_t k, int n, int* x) {
  * first position.  Then toggle x_j.  Returns j (1-based). --------------- */
 static int nextset(int* t, int* x, int n) {
   int j = 1;
-  *t = -*t;
+  if (!MUT(2)) *t = -*t;
   if (*t == 1) {
     while (j <= n && x[j] == 0) ++j;
     j = j + 1;
@@ -184,8 +194,10 @@ int oracle_glynn_range_c(const double* A, int n, uint64_t first, uint64_t count,
   for (int i = 0; i < n; ++i) {
     ld rr = 0, ri = 0;
     for (int j = 0; j < n; ++j) rr += RE(A, n, i, j), ri += IM(A, n, i, j);
-    wr[i] = RE(A, n, i, n - 1) - rr / 2;
-    wi[i] = IM(A, n, i, n - 1) - ri / 2;
+    const int jn = MUT(3) ? 0 : n - 1;
+    const ld half = MUT(5) ? 1 : 2;
+    wr[i] = RE(A, n, i, jn) - rr / half;
+    wi[i] = IM(A, n, i, jn) - ri / half;
   }
   /* steps 6-8: add the columns j < n whose bit x_j is set */
   for (int j = 1; j <= n - 1; ++j)
@@ -194,7 +206,7 @@ int oracle_glynn_range_c(const double* A, int n, uint64_t first, uint64_t count,
   /* steps 9-15 */
   for (uint64_t step = 0; step < count; ++step) {
     ld pr = 1, pi = 0; /* step 10: p := prod_i w_i */
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < n - (MUT(1) ? 1 : 0); ++i) {
       ld nr = pr * wr[i] - pi * wi[i], ni = pr * wi[i] + pi * wr[i];
       pr = nr, pi = ni;
     }
@@ -203,8 +215,10 @@ int oracle_glynn_range_c(const double* A, int n, uint64_t first, uint64_t count,
     csum_add(&si, t * pi);
     if (abs_sum) csum_add(&sa, sqrtl(pr * pr + pi * pi));
     int z = 2 * x[j] - 1; /* step 13 */
-    for (int i = 0; i < n; ++i) /* step 14: w_i := w_i + z a_{i,j} */
-      wr[i] += z * RE(A, n, i, j - 1), wi[i] += z * IM(A, n, i, j - 1);
+    for (int i = 0; i < n; ++i) { /* step 14: w_i := w_i + z a_{i,j} */
+      const int ri_ = MUT(4) ? j - 1 : i, cj_ = MUT(4) ? i : j - 1;
+      wr[i] += z * RE(A, n, ri_, cj_), wi[i] += z * IM(A, n, ri_, cj_);
+    }
   }
   out[0] = csum_value(&sr);
   out[1] = csum_value(&si);
@@ -243,7 +257,7 @@ int oracle_per_glynn_c(const double* A, int n, int m, int threads, ld* out, ld* 
     csum_add(&sa, part[3 * k + 2]);
   }
   free(part);
-  ld s = (n & 1) ? -2 : 2;
+  ld s = ((n & 1) != MUT(6)) ? -2 : 2;
   out[0] = s * csum_value(&sr);
   out[1] = s * csum_value(&si);
   if (abs_sum) *abs_sum = 2 * csum_value(&sa);
