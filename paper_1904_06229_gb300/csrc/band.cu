@@ -7,9 +7,11 @@
 // Layout: one CTA per matrix.  Row i's linear form only involves the 2k+1
 // variables x_{i-k}..x_{i+k} (the window), so the polynomial is stored densely
 // over the 2^(2k+1) subsets of the window, in shared memory (k <= 5: 2048
-// complex coefficients, two buffers).  Multiplying by C_i is written in gather
-// form, q[T] = sum_{t in T} p[T - t] a_{i, base+t}, so every coefficient is
-// produced by one thread in a fixed order (deterministic, no atomics).
+// complex coefficients, two buffers), of which only the subsets of the one
+// size a live monomial can have are formed.  Multiplying by C_i is written in
+// gather form, q[T] = sum_{t in T} p[T - t] a_{i, base+t}, so every
+// coefficient is produced by one thread in a fixed order (deterministic, no
+// atomics).
 // Retiring the window's lowest variable keeps the monomials that contain it
 // (with the variable set to 1, as in App. C) and shifts the window by one;
 // monomials without it can never reach full degree, so they are dropped
@@ -29,6 +31,10 @@ namespace perm {
 constexpr int kBandThreads = 256;
 constexpr int kBandKMax = 5;
 
+// Before row i is multiplied in, every live monomial holds all retired
+// variables and min(i, K) window variables; after it, min(i, K) + 1.  Only the
+// window subsets of that size are formed (C(2K+1, K+1) of 2^(2K+1) at K = 5);
+// entries of other sizes are never read.
 template <int K>
 __global__ void __launch_bounds__(kBandThreads) k_band(const double* __restrict__ Ag, int n,
                                                        double* __restrict__ out, int* __restrict__ status) {
@@ -38,13 +44,27 @@ __global__ void __launch_bounds__(kBandThreads) k_band(const double* __restrict_
   double2* p = bsmem;
   double2* q = p + S;
   double2* coef = q + S;
+  __shared__ unsigned short ord[S];  // window subsets sorted by size
+  __shared__ int off[W + 2];         // subsets of size c are ord[off[c] .. off[c+1])
   __shared__ dd red[2 * (kBandThreads / 32)];
   const double2* A = reinterpret_cast<const double2*>(Ag) + (size_t)blockIdx.x * n * n;
 
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int c = 0; c <= W; ++c) {
+      off[c] = o;
+      for (int m = 0; m < S; ++m)
+        if (__popc(m) == c) ord[o++] = (unsigned short)m;
+    }
+    off[W + 1] = o;
+  }
   for (int m = threadIdx.x; m < S; m += kBandThreads) p[m] = make_double2(m == 0 ? 1.0 : 0.0, 0.0);
+  __syncthreads();
   int bad = 0;
+  int deg = 0;  // size of the live subsets after the current row
   for (int i = 0; i < n; ++i) {
     const int base = i - K;  // variable index of window bit 0
+    deg = (i < K ? i : K) + 1;
     if (threadIdx.x < W) {
       const int j = base + (int)threadIdx.x;
       double2 a = make_double2(0.0, 0.0);
@@ -55,8 +75,9 @@ __global__ void __launch_bounds__(kBandThreads) k_band(const double* __restrict_
       coef[threadIdx.x] = a;
     }
     __syncthreads();
-    // q = p * C_i with x_j^2 = 0
-    for (int T = threadIdx.x; T < S; T += kBandThreads) {
+    // q = p * C_i with x_j^2 = 0, on the subsets of size deg
+    for (int t2 = off[deg] + threadIdx.x; t2 < off[deg + 1]; t2 += kBandThreads) {
+      const int T = ord[t2];
       double qr = 0.0, qi = 0.0;
 #pragma unroll
       for (int t = 0; t < W; ++t) {
@@ -77,7 +98,10 @@ __global__ void __launch_bounds__(kBandThreads) k_band(const double* __restrict_
       // the new top bit (x_{i+1+K}) has not been multiplied in yet
       for (int Sn = threadIdx.x; Sn < S; Sn += kBandThreads) {
         double2 v = make_double2(0.0, 0.0);
-        if (!((Sn >> (W - 1)) & 1)) v = base >= 0 ? q[(Sn << 1) | 1] : q[Sn << 1];
+        if (!((Sn >> (W - 1)) & 1)) {
+          const int T = base >= 0 ? ((Sn << 1) | 1) : (Sn << 1);
+          if (__popc(T) == deg) v = q[T];
+        }
         p[Sn] = v;
       }
       __syncthreads();
@@ -86,7 +110,8 @@ __global__ void __launch_bounds__(kBandThreads) k_band(const double* __restrict_
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, (int)kStatusNonFinite);
   // all x := 1: sum of the coefficients (only the full monomial survives)
   dd sr{0.0, 0.0}, si{0.0, 0.0};
-  for (int T = threadIdx.x; T < S; T += kBandThreads) {
+  for (int t2 = off[deg] + threadIdx.x; t2 < off[deg + 1]; t2 += kBandThreads) {
+    const int T = ord[t2];
     sr = dd_add_d(sr, q[T].x);
     si = dd_add_d(si, q[T].y);
   }
