@@ -328,6 +328,7 @@ def run_gpu(args):
         line["exact"] = exact_measure(P, torch, dev)
         line["precision"] = precision_measure(P, torch, dev)
         line["next_rows"] = next_rows_measure(P, torch, dev)
+        line["stats"] = stats_measure(P, torch, dev)
     if rank == 0 and not args.no_cpu_baseline:
         cb, (first, count, g) = cpu_oracle_sample(A)
         line["cpu_baseline"] = cb
@@ -427,6 +428,31 @@ def next_rows_measure(P, torch, dev):
     t_b, _ = _timed(torch, lambda: P.perm_c128_band(tB, 5).cpu())
     out["band_n100_k5_x1000"] = {"seconds": t_b, "matrices_per_s": 1000 / t_b}
     return out
+
+
+def stats_measure(P, torch, dev, per_order: int = 500):
+    """Sec. 4 circular-entry study on a sample: per order n = 8..16, `per_order`
+    matrices with entries exp(i theta), statistics of X = |per| / sqrt(n!) from
+    perm_batch_stats (one graph launch plus the statistics kernel)."""
+    from paper_1904_06229_gb300 import workloads as W
+
+    mats, seed = [], 0
+    for n in range(8, 17):
+        for _ in range(per_order):
+            mats.append(torch.from_numpy(W.circular(n, 500_000 + seed)).to(dev))
+            seed += 1
+    P.perm_batch_stats(mats)  # tunes, captures the graph
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    _, st = P.perm_batch_stats(mats)
+    e1.record()
+    torch.cuda.synchronize()
+    st = st.cpu().numpy()
+    per_n = {str(n): {"count": int(st[n, 0]), "mean_X": st[n, 1] / st[n, 0], "mean_X2": st[n, 2] / st[n, 0]}
+             for n in range(8, 17)}
+    return {"family": "circular exp(i theta)", "matrices": len(mats), "seconds": e0.elapsed_time(e1) / 1e3,
+            "per_order": per_n}
 
 
 def batch_measure(P, torch, dev, sample):
