@@ -364,6 +364,8 @@ def exact_measure(P, torch, dev):
     four 62-bit primes, CRT on the host."""
     from paper_1904_06229_gb300 import workloads as W
 
+    import os
+
     primes = P.perm_default_primes()
     out = {}
     for n, seed in ((30, 6), (36, 7)):
@@ -371,8 +373,21 @@ def exact_measure(P, torch, dev):
         res = torch.empty(4, dtype=torch.int64, device=dev)
         sec, _ = _timed(torch, lambda: P.perm_mod01(t, primes, res))
         val = P.perm_crt([int(v) for v in res.cpu()], primes)
+        # the same residues through the modular group walk (no exact sums)
+        old = os.environ.get("PERM_MOD_SUM")
+        os.environ["PERM_MOD_SUM"] = "modular"
+        try:
+            res_m = torch.empty(4, dtype=torch.int64, device=dev)
+            sec_m, _ = _timed(torch, lambda: P.perm_mod01(t, primes, res_m), reps=1)
+        finally:
+            if old is None:
+                del os.environ["PERM_MOD_SUM"]
+            else:
+                os.environ["PERM_MOD_SUM"] = old
         out[f"n{n}"] = {"seconds": sec, "codes_per_s": (1 << (n - 1)) / sec, "per_bits": val.bit_length(),
-                        "per_mod_1e9+7": val % 1000000007}
+                        "per_mod_1e9+7": val % 1000000007,
+                        "modular_walk": {"seconds": sec_m, "codes_per_s": (1 << (n - 1)) / sec_m,
+                                         "same_residues": res_m.cpu().tolist() == res.cpu().tolist()}}
     return out
 
 

@@ -199,7 +199,9 @@ int perm_batch_autotune(int n_lo, int n_hi);
  *   2^(n-1) per(A) = (-1)^(n-1) sum_r (-1)^r prod_i v_i(x(r)),
  *   v_i(x) = 2 a_{i,n} - sum_j a_{i,j} + 2 sum_{j<n, x_j=1} a_{i,j},
  * evaluated modulo each of four odd primes below 2^62 (64-bit Montgomery
- * arithmetic), then multiplied by (-1)^(n-1) / 2^(n-1) mod p.
+ * arithmetic), then multiplied by (-1)^(n-1) / 2^(n-1) mod p.  Any odd
+ * moduli in [3, 2^62) give correct residues; the fastest grouping of the
+ * exact row products needs moduli above (max_i sum_j |a_ij|)^4.
  * A: n*n int8 entries (any value, |a| <= 127).  primes: HOST array of 4
  * distinct odd moduli in [3, 2^62) (primality is the caller's promise; see
  * perm_default_primes).  residues: 4 uint64, per(A) mod primes[q] in [0, p).

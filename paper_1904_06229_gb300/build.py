@@ -36,6 +36,9 @@ SOURCES = [
     "walk_fx_r64_f32.cu",
     "walk_df_c128.cu",
     "glynn_mod.cu",
+    "mod_lo.cu",
+    "mod_mid.cu",
+    "mod_hi.cu",
     "ryser2.cu",
     "band.cu",
     "sparse.cu",

@@ -1,0 +1,13 @@
+// Instantiations of the exact-integer / modular walk, orders 1..32.
+#include "glynn_mod.cuh"
+
+namespace perm {
+
+int mod_resident_lo(int n) { return mod_resident_dispatch<1, 32>(n); }
+
+cudaError_t mod_launch_lo(int n, const int8_t* A, const ModConsts& c, uint64_t count, uint64_t* partials, int blocks,
+                          cudaStream_t s) {
+  return mod_launch_dispatch<1, 32>(n, A, c, count, partials, blocks, s);
+}
+
+}  // namespace perm

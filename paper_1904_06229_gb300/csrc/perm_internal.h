@@ -82,21 +82,25 @@ cudaError_t finalize_launch(const double* partials, int nparts, bool cplx, int n
                             cudaStream_t stream);
 
 // ---- modular path ----
-struct ModArgs {
-  const int8_t* A;
-  int n;
-  uint64_t p[4];       // moduli
-  uint64_t pinv[4];    // -p^{-1} mod 2^64
-  uint64_t r2[4];      // 2^128 mod p (Montgomery R^2)
-  uint64_t one[4];     // 2^64 mod p (Montgomery form of 1)
-  uint64_t scale[4];   // (-1)^(n-1) / 2^(n-1) mod p, plain form
-  uint64_t* partials;  // blocks x 4 residues (plain form)
-  int blocks;
-  uint64_t* residues;  // device, 4
-  cudaStream_t stream;
+// Constants of the Montgomery walk (glynn_mod.cuh) for four odd moduli.
+struct ModConsts {
+  uint64_t p[4];
+  uint64_t pinv[4];        // -p^-1 mod 2^64
+  uint64_t r2[4];          // R^2 mod p, R = 2^64
+  uint64_t fix[3][2][4];   // [G = 12, 8, 4][first group reduced through R^2, or not][q]: R^(groups - 1 + k) mod p
+  uint64_t rpow[4][4];     // [w][q]: R^w mod p (w = 0..3), for reducing a 256-bit integer
+  uint64_t pmin;           // smallest modulus
+  int exact_ok;            // 0: always take the modular group walk (PERM_MOD_SUM=modular)
 };
-int mod_resident_blocks(int n);
-cudaError_t mod_launch(const ModArgs& a);
+int mod_resident_lo(int n);   // n in 1..32
+int mod_resident_mid(int n);  // n in 33..48
+int mod_resident_hi(int n);   // n in 49..64
+cudaError_t mod_launch_lo(int n, const int8_t* A, const ModConsts& c, uint64_t count, uint64_t* partials, int blocks,
+                          cudaStream_t s);
+cudaError_t mod_launch_mid(int n, const int8_t* A, const ModConsts& c, uint64_t count, uint64_t* partials, int blocks,
+                           cudaStream_t s);
+cudaError_t mod_launch_hi(int n, const int8_t* A, const ModConsts& c, uint64_t count, uint64_t* partials, int blocks,
+                          cudaStream_t s);
 
 // ---- batch path ----
 struct BatchItem {

@@ -12,6 +12,20 @@ pytestmark = pytest.mark.gpu
 
 PRIMES = O.default_primes()
 
+# The kernel sums exactly in 192- or 256-bit integers where the bound allows
+# it and otherwise multiplies row groups modulo each prime; PERM_MOD_SUM=modular
+# forces the second form so both are checked at the same sizes.
+SUMS = ["auto", "modular"]
+
+
+@pytest.fixture(params=SUMS)
+def mod_sum(request, monkeypatch):
+    if request.param == "modular":
+        monkeypatch.setenv("PERM_MOD_SUM", "modular")
+    else:
+        monkeypatch.delenv("PERM_MOD_SUM", raising=False)
+    return request.param
+
 
 def gpu_mod(A, primes=PRIMES):
     t = torch.from_numpy(np.ascontiguousarray(np.asarray(A, dtype=np.int8))).cuda()
@@ -24,7 +38,7 @@ def gpu_exact(A):
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 7, 8, 9, 12, 16, 17, 20])
-def test_zero_one_and_pm1_exact(n):
+def test_zero_one_and_pm1_exact(n, mod_sum):
     for A in (W.zero_one(n, 600 + n), W.bernoulli_pm1(n, 650 + n)):
         ex = O.per_exact(A)
         assert gpu_mod(A) == [ex % p for p in PRIMES]
@@ -32,7 +46,7 @@ def test_zero_one_and_pm1_exact(n):
 
 
 @pytest.mark.parametrize("n", [5, 9, 13])
-def test_general_int8_exact(n):
+def test_general_int8_exact(n, mod_sum):
     """Entries up to +-127 take the 4-row grouping of the exact products."""
     A = np.random.default_rng(n).integers(-127, 128, (n, n)).astype(np.int8)
     ex = O.per_exact(A)
@@ -40,7 +54,7 @@ def test_general_int8_exact(n):
     assert gpu_mod(A) == O.per_mod(A, PRIMES)
 
 
-def test_closed_forms():
+def test_closed_forms(mod_sum):
     for n in (10, 20, 25):
         J = np.ones((n, n), dtype=np.int8)
         import math
@@ -57,6 +71,80 @@ def test_other_moduli():
     A = W.zero_one(14, 3)
     ps = O.largest_primes_below(1 << 40, 4)
     assert gpu_mod(A, ps) == O.per_mod(A, ps)
+
+
+@pytest.mark.parametrize(
+    "moduli",
+    [
+        [3, 5, 7, 11],  # every group product exceeds the moduli
+        [1000003, 999983, 65537, 257],
+        "below 2^40",
+        "below 2^52",
+    ],
+)
+@pytest.mark.parametrize("kind", ["zero_one", "pm1", "int8", "small"])
+def test_moduli_smaller_than_group_products(moduli, kind, mod_sum):
+    """Any odd moduli below 2^62 are accepted; where a row group's product can
+    exceed the smallest modulus the kernel reduces groups through R^2.  The
+    residues are compared with the exact permanent reduced in Python."""
+    if moduli == "below 2^40":
+        moduli = O.largest_primes_below(1 << 40, 4)
+    elif moduli == "below 2^52":
+        moduli = O.largest_primes_below(1 << 52, 4)
+    n = 13
+    rng = np.random.default_rng(len(kind) * 7 + n)
+    A = {
+        "zero_one": W.zero_one(n, 91),
+        "pm1": W.bernoulli_pm1(n, 92),
+        # n = 24 with entries up to 127: sums need more than 256 bits, so
+        # this one takes the modular group walk even without the override
+        "int8": np.random.default_rng(24).integers(-127, 128, (24, 24)).astype(np.int8),
+        "small": rng.integers(0, 4, (n, n)).astype(np.int8),
+    }[kind]
+    ex = O.per_exact(A)
+    assert gpu_mod(A, moduli) == [ex % p for p in moduli]
+
+
+@pytest.mark.parametrize("n", [1, 2, 11, 12, 13, 24, 25])
+def test_group_size_boundaries(n, mod_sum):
+    """Orders on both sides of the 12-, 8- and 4-row groups; entries 0..3 make
+    rows sums up to 3n, so the 8-row grouping is taken where 12 rows would
+    overflow the moduli."""
+    A = np.random.default_rng(500 + n).integers(0, 4, (n, n)).astype(np.int8)
+    ex = O.per_exact(A)
+    assert gpu_mod(A) == [ex % p for p in PRIMES]
+    assert gpu_exact(A) == ex
+
+
+def test_exact_sum_widths():
+    """Cases for each exact-sum form: 256-bit sums with 6-row int32 factors
+    (all-ones and J - I at n = 35: n! and the derangement number), 256-bit sums
+    with 2-row factors (entries up to 127, n = 20), 192-bit with 2-row factors
+    (n = 12)."""
+    import math
+
+    J = np.ones((35, 35), dtype=np.int8)
+    assert gpu_exact(J) == math.factorial(35)
+    D = [1, 0]
+    for k in range(2, 36):
+        D.append((k - 1) * (D[-1] + D[-2]))
+    assert gpu_exact(J - np.eye(35, dtype=np.int8)) == D[35]
+    for n in (12, 20):
+        A = np.random.default_rng(700 + n).integers(-127, 128, (n, n)).astype(np.int8)
+        ex = O.per_exact(A)
+        assert gpu_mod(A) == [ex % p for p in PRIMES]
+        assert gpu_exact(A) == ex
+
+
+def test_both_sums_agree_n28(monkeypatch):
+    """0-1 n = 28: the exact-integer sum and the modular group walk give the
+    same residues."""
+    A = W.zero_one(28, 13)
+    monkeypatch.delenv("PERM_MOD_SUM", raising=False)
+    a = gpu_mod(A)
+    monkeypatch.setenv("PERM_MOD_SUM", "modular")
+    b = gpu_mod(A)
+    assert a == b
 
 
 def test_config_n30_zero_one():
