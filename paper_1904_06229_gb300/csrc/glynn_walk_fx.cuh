@@ -35,8 +35,12 @@ namespace perm {
 template <int N, bool CPLX>
 struct FxShape {
   static constexpr int E = CPLX ? 2 : 1;
+  // Column stride of the tables: an odd number of entries, so that the columns
+  // that the threads of a warp read at once (each at its own Gray code) start
+  // in different shared-memory banks.
+  static constexpr int S = N | 1;
   // +2A and -2A tables (int64, column-major), v0 (int64), per-row exponent bias (int), dd reduction slots
-  static constexpr size_t table_bytes = (size_t)N * N * E * sizeof(long long);
+  static constexpr size_t table_bytes = (size_t)N * S * E * sizeof(long long);
   static constexpr size_t smem_bytes = 2 * table_bytes + (size_t)N * E * sizeof(long long) + N * sizeof(int) +
                                        8 * sizeof(dd) + 16;
 };
@@ -190,6 +194,7 @@ template <int N, bool CPLX>
 __device__ __forceinline__ bool fx_stage(const double* __restrict__ A, long long* sP, long long* sM, long long* sV0,
                                          int* sEb, int* sF, int* status) {
   constexpr int E = CPLX ? 2 : 1;
+  constexpr int S = FxShape<N, CPLX>::S;
   int bad = 0;
   if (threadIdx.x < N) {
     const int i = threadIdx.x;
@@ -223,8 +228,8 @@ __device__ __forceinline__ bool fx_stage(const double* __restrict__ A, long long
 #pragma unroll
     for (int c = 0; c < E; ++c) {
       const long long q = __double2ll_rn(scalbn(A[(size_t)idx * E + c], F));
-      sP[(j * N + i) * E + c] = 2 * q;
-      sM[(j * N + i) * E + c] = -2 * q;
+      sP[(j * S + i) * E + c] = 2 * q;
+      sM[(j * S + i) * E + c] = -2 * q;
     }
   }
   __syncthreads();
@@ -233,8 +238,8 @@ __device__ __forceinline__ bool fx_stage(const double* __restrict__ A, long long
 #pragma unroll
     for (int c = 0; c < E; ++c) {
       // v0_i = A_{i,n} - sum_{j<n} A_ij  (all e_j = -1), from the doubled table
-      long long s = sP[((N - 1) * N + i) * E + c];
-      for (int j = 0; j < N - 1; ++j) s -= sP[(j * N + i) * E + c];
+      long long s = sP[((N - 1) * S + i) * E + c];
+      for (int j = 0; j < N - 1; ++j) s -= sP[(j * S + i) * E + c];
       sV0[i * E + c] = s / 2;
     }
   }
@@ -243,8 +248,9 @@ __device__ __forceinline__ bool fx_stage(const double* __restrict__ A, long long
 }
 
 // TWO_TABLES: read -2A from its own table; otherwise negate +2A on the fly
-// (integer ops only; used where shared memory is tight).
-template <int N, int MODE, bool TWO_TABLES = true>
+// (integer ops only; used where shared memory is tight).  ST: column stride
+// of the tables in entries.
+template <int N, int MODE, bool TWO_TABLES = true, int ST = N>
 __device__ __forceinline__ void thread_walk_c128_fx(const longlong2* __restrict__ sP, const longlong2* __restrict__ sM,
                                                     const longlong2* __restrict__ sV0, const int* __restrict__ sEb,
                                                     uint64_t r, const uint64_t end, dd& accr, dd& acci) {
@@ -261,7 +267,7 @@ __device__ __forceinline__ void thread_walk_c128_fx(const longlong2* __restrict_
 #pragma unroll 1
       for (int j = 0; j < N - 1; ++j) {
         if ((x >> j) & 1ull) {
-          const longlong2 c = sP[j * N + i];
+          const longlong2 c = sP[j * ST + i];
           v.x += c.x;
           v.y += c.y;
         }
@@ -289,7 +295,7 @@ __device__ __forceinline__ void thread_walk_c128_fx(const longlong2* __restrict_
       uint32_t neg;
       gray_step(r, j, neg);
       if constexpr (TWO_TABLES) {
-        const longlong2* col = (neg ? sM : sP) + j * N;
+        const longlong2* col = (neg ? sM : sP) + j * ST;
 #pragma unroll
         for (int i = 0; i < N; ++i) {
           const longlong2 c = col[i];
@@ -297,7 +303,7 @@ __device__ __forceinline__ void thread_walk_c128_fx(const longlong2* __restrict_
           vi[i] += c.y;
         }
       } else {
-        const longlong2* col = sP + j * N;
+        const longlong2* col = sP + j * ST;
         const long long m = -(long long)neg;  // 0 or all ones
 #pragma unroll
         for (int i = 0; i < N; ++i) {
@@ -357,7 +363,7 @@ __device__ __forceinline__ bool fx_stage_warp_c128(const double2* __restrict__ A
   return false;
 }
 
-template <int N, int MODE>
+template <int N, int MODE, int ST = N>
 __device__ __forceinline__ void thread_walk_r64_fx(const long long* __restrict__ sP, const long long* __restrict__ sM,
                                                    const long long* __restrict__ sV0, const int* __restrict__ sEb,
                                                    uint64_t r, const uint64_t end, dd& accr) {
@@ -372,7 +378,7 @@ __device__ __forceinline__ void thread_walk_r64_fx(const long long* __restrict__
       long long s = sV0[i];
 #pragma unroll 1
       for (int j = 0; j < N - 1; ++j)
-        if ((x >> j) & 1ull) s += sP[j * N + i];
+        if ((x >> j) & 1ull) s += sP[j * ST + i];
       seed[i] = s;
     }
 #pragma unroll
@@ -390,7 +396,7 @@ __device__ __forceinline__ void thread_walk_r64_fx(const long long* __restrict__
       int j;
       uint32_t neg;
       gray_step(r, j, neg);
-      const long long* col = (neg ? sM : sP) + j * N;
+      const long long* col = (neg ? sM : sP) + j * ST;
 #pragma unroll
       for (int i = 0; i < N; ++i) v[i] += col[i];
     }
@@ -403,10 +409,11 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk_fx(const double* __restri
                                                           double* __restrict__ partials, int accumulate,
                                                           int* __restrict__ status) {
   constexpr int E = CPLX ? 2 : 1;
+  constexpr int S = FxShape<N, CPLX>::S;
   extern __shared__ __align__(16) long long fsm[];
   long long* sP = fsm;
-  long long* sM = sP + N * N * E;
-  long long* sV0 = sM + N * N * E;
+  long long* sM = sP + N * S * E;
+  long long* sV0 = sM + N * S * E;
   int* sEb = reinterpret_cast<int*>(sV0 + N * E);
   int* sF = sEb + N;
   dd* sRed = reinterpret_cast<dd*>(fsm) ;  // reused after the walk (tables no longer read)
@@ -418,10 +425,11 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk_fx(const double* __restri
   dd accr{0.0, 0.0}, acci{0.0, 0.0};
   if (!bad) {
     if constexpr (CPLX)
-      thread_walk_c128_fx<N, MODE>(reinterpret_cast<const longlong2*>(sP), reinterpret_cast<const longlong2*>(sM),
-                                   reinterpret_cast<const longlong2*>(sV0), sEb, r, end, accr, acci);
+      thread_walk_c128_fx<N, MODE, true, S>(reinterpret_cast<const longlong2*>(sP),
+                                            reinterpret_cast<const longlong2*>(sM),
+                                            reinterpret_cast<const longlong2*>(sV0), sEb, r, end, accr, acci);
     else
-      thread_walk_r64_fx<N, MODE>(sP, sM, sV0, sEb, r, end, accr);
+      thread_walk_r64_fx<N, MODE, S>(sP, sM, sV0, sEb, r, end, accr);
   } else {
     accr = dd{__longlong_as_double(0x7ff8000000000000ll), 0.0};
     acci = accr;
