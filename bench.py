@@ -324,6 +324,8 @@ def run_gpu(args):
         os.environ["PERM_ROWS"] = rows
     if rank == 0 and args.batch_sample > 0:
         line["batch"] = batch_measure(P, torch, dev, args.batch_sample)
+    if rank == 0 and args.batch_study > 0:
+        line["batch_study"] = batch_study_measure(P, torch, dev, args.batch_study)
     if rank == 0 and not args.no_extras:
         line["exact"] = exact_measure(P, torch, dev)
         line["precision"] = precision_measure(P, torch, dev)
@@ -506,6 +508,55 @@ def batch_measure(P, torch, dev, sample):
             "max_abs_diff_vs_per_launch": d, "max_abs_value": scale, "gpu_launches_batched": 2}
 
 
+def batch_study_measure(P, torch, dev, count):
+    """The whole batch study in one persistent launch: `count` matrices (n ~
+    U{12..28}, half Gaussian, half Haar S(n^2, n), shuffled; seed 3) through
+    perm_batch_stats, with the per-order moments of X = |per| / sqrt(n!), and
+    64 results checked against single perm_c128 launches."""
+    from paper_1904_06229_gb300 import workloads as W
+
+    t0 = time.time()
+    ns, mats = W.batch_study(count, seed=3)
+    gen_s = time.time() - t0
+    offs = np.concatenate([[0], np.cumsum([m.size for m in mats])]).astype(np.int64)
+    flat = np.empty(int(offs[-1]), dtype=np.complex128)
+    for k, m in enumerate(mats):
+        flat[offs[k]:offs[k + 1]] = m.ravel()
+    del mats
+    dflat = torch.from_numpy(flat).to(dev)
+    dm = [dflat[int(offs[k]):int(offs[k + 1])].view(int(ns[k]), int(ns[k])) for k in range(count)]
+    ptrs = torch.tensor([t.data_ptr() for t in dm], dtype=torch.int64, device=dev)
+    terms = int(sum(1 << (int(n) - 1) for n in ns))
+    P.perm_batch_autotune(int(ns.min()), int(ns.max()))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0 = time.time()
+    e0.record()
+    out, stats = P.perm_batch_stats(dm, ptrs=ptrs)  # plan (item list, graph) built on the host, then one launch
+    plan_s = time.time() - h0
+    e1.record()
+    torch.cuda.synchronize()
+    total_s = e0.elapsed_time(e1) / 1e3
+    status = P.perm_last_status()
+    rng = np.random.default_rng(1)
+    worst = 0.0
+    for k in rng.choice(count, 64, replace=False):
+        ref = P.perm_c128(dm[int(k)]).cpu().numpy()
+        got = out[int(k)].cpu().numpy()
+        worst = max(worst, float(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)))
+    st = stats.cpu().numpy()
+    per_n = {}
+    for n in range(int(ns.min()), int(ns.max()) + 1):
+        c = float(st[n, 0])
+        if c > 0:
+            per_n[str(n)] = {"count": int(c), "mean_X": st[n, 1] / c, "mean_X2": st[n, 2] / c, "mean_X4": st[n, 4] / c}
+    kernel_s = total_s - plan_s
+    return {"matrices": count, "orders": "12..28", "terms": terms, "generate_s": gen_s,
+            "seconds_incl_host_plan": total_s, "host_plan_s": plan_s, "perms_per_s": count / kernel_s,
+            "terms_per_s": terms / kernel_s, "status": status, "max_rel_diff_vs_perm_c128_64": worst,
+            "per_order": per_n}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -513,6 +564,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--batch-sample", type=int, default=2000)
+    ap.add_argument("--batch-study", type=int, default=0,
+                    help="also run the whole batch study (e.g. 200000 matrices) in one launch; minutes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-alt-rows", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the exact-path and precision measurements")

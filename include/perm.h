@@ -54,12 +54,20 @@ typedef enum {
 } perm_status;
 
 /* ---- FP64 permanents (Sec. 2.A, App. A; precision scheme of Sec. 2.B) ----
- * Row sums w_i and products in FP64, one fused multiply-add per row-sum update;
- * each thread's terms are summed in FP64 over runs of at most 4096 codes and
- * folded into a double-double accumulator; runs restart w from its
- * definition (bounding incremental drift); the per-thread accumulators are
- * combined with warp shuffles and a fixed-order tree in double-double.
- * out: the permanent, double-double rounded to double(s). */
+ * Row sums are held exactly as 64-bit fixed-point integers (each row scaled by
+ * a power of two, 2^F_i with F_i = 61 - floor(log2 max(sum_j |Re a_ij|,
+ * sum_j |Im a_ij|)), entries rounded to that grid once), so the Gray-step
+ * updates are exact integer additions and never drift; each factor is turned
+ * into a double by integer bit operations and the products are formed in FP64
+ * (fused multiply-adds).  Each thread's terms are summed in FP64 over runs of
+ * at most 4096 codes and folded into a double-double accumulator; the per-
+ * thread accumulators are combined with warp shuffles and a fixed-order tree
+ * in double-double.  out: the permanent, double-double rounded to double(s).
+ * The environment variable PERM_ROWS selects another row arithmetic for these
+ * entry points: "fp64" (FP64 row sums, one fused multiply-add per update,
+ * restarted from their definition every 4096 codes to bound drift) or "df"
+ * (complex only: row sums and products as pairs of FP32 on the FP32 pipe,
+ * restarted from the exact integer row sums every 128 codes). */
 
 /* Complex permanent. A: 2*n*n doubles (interleaved). out: 2 doubles (re, im). */
 int perm_c128(const double* A, int n, double* out, void* stream);
@@ -171,7 +179,9 @@ int perm_sparse_partition(const double* A_host, int n, int* block, uint64_t* cou
  * in a CUDA graph keyed by (ns, count) and replayed on later calls with the
  * same sizes.  Chunk lengths come from a per-(GPU, n) tuning table that the
  * library fills by timing candidates the first time an order is seen (see
- * perm_batch_autotune).  Results equal perm_c128 on the same matrix to within
+ * perm_batch_autotune; PERM_BATCH_TUNE=0 in the environment takes the
+ * default length without timing, as does a call made while `stream` is
+ * being captured).  Results equal perm_c128 on the same matrix to within
  * rounding of the summation order. */
 int perm_batch(const double* const* ptrs, const int* ns, int count, double* out, void* stream);
 
@@ -198,10 +208,15 @@ int perm_batch_autotune(int n_lo, int n_hi);
  * Glynn's form (the App. A sum with v = 2w, an integer for integer A):
  *   2^(n-1) per(A) = (-1)^(n-1) sum_r (-1)^r prod_i v_i(x(r)),
  *   v_i(x) = 2 a_{i,n} - sum_j a_{i,j} + 2 sum_{j<n, x_j=1} a_{i,j},
- * evaluated modulo each of four odd primes below 2^62 (64-bit Montgomery
- * arithmetic), then multiplied by (-1)^(n-1) / 2^(n-1) mod p.  Any odd
- * moduli in [3, 2^62) give correct residues; the fastest grouping of the
- * exact row products needs moduli above (max_i sum_j |a_ij|)^4.
+ * evaluated modulo each of four odd primes below 2^62, then multiplied by
+ * (-1)^(n-1) / 2^(n-1) mod p.  Row sums v_i are exact int32.  Where every
+ * per-thread partial sum is provably below 2^255 (bound: codes per thread
+ * times prod_i sum_j |a_ij|; 0-1 and +-1 matrices up to n of about 40), each
+ * thread sums its terms exactly as a multi-limb integer and reduces that sum
+ * modulo the primes once; otherwise exact products of row groups are combined
+ * modulo each prime per term (64-bit Montgomery arithmetic).  The environment
+ * variable PERM_MOD_SUM=modular forces the second form (same residues).  Any
+ * odd moduli in [3, 2^62) give correct residues.
  * A: n*n int8 entries (any value, |a| <= 127).  primes: HOST array of 4
  * distinct odd moduli in [3, 2^62) (primality is the caller's promise; see
  * perm_default_primes).  residues: 4 uint64, per(A) mod primes[q] in [0, p).
@@ -236,7 +251,10 @@ const char* perm_status_string(int status);
 int perm_fp64_peak(double* gops);
 
 /* Free the library's per-device status words, cached graphs and the stream-
- * ordered memory pool's unused reserve.  Safe to call more than once. */
+ * ordered memory pool's unused reserve.  Safe to call more than once; the
+ * next compute call allocates afresh.  Call it with no work of the library in
+ * flight, and launch no graph captured earlier from this library's calls
+ * afterwards (such graphs hold the freed status word). */
 void perm_shutdown(void);
 
 #ifdef __cplusplus

@@ -152,6 +152,16 @@ cudaError_t band_dispatch(int k, const double* A, int n, int count, double* out,
   }
 }
 
+template <int LO, int HI>
+void band_preload() {
+  if constexpr (LO <= HI) {
+    load_kernel(k_band<LO>);
+    band_preload<LO + 1, HI>();
+  }
+}
+
+void preload_band_kernels() { band_preload<0, kBandKMax>(); }
+
 }  // namespace perm
 
 namespace {
@@ -177,6 +187,7 @@ extern "C" int perm_c128_band(const double* A, int n, int k, int count, double* 
     return PERM_ECUDA;
   }
   if (cudaGetDevice(&dev) != cudaSuccess) return PERM_ECUDA;
+  ensure_kernels_loaded();
   int* status = nullptr;
   if (device_status_word(dev, &status) != 0) return PERM_ECUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -17,6 +17,8 @@
 // perm_batch_autotune); PERM_BATCH_TUNE=0 keeps the built-in default.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -149,7 +151,7 @@ __global__ void k_batch_finalize(const double* __restrict__ item_partials, const
 
 template <int ROWS>
 int batch_resident_blocks_t() {
-  static int cached[64] = {0};
+  static std::atomic<int> cached[64];  // per device; filled once, read from any host thread
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
   if (cached[dev]) return cached[dev];
@@ -242,6 +244,11 @@ __global__ void __launch_bounds__(256) k_batch_stats(const double* __restrict__ 
   for (int b = threadIdx.x; b <= kStatsEdges; b += blockDim.x) st[5 + b] = (double)hist[b];
 }
 
+void preload_batch_kernels() {
+  load_kernel(k_batch_finalize);
+  load_kernel(k_batch_stats);
+}
+
 }  // namespace perm
 
 using namespace perm;
@@ -314,6 +321,34 @@ void build_items(const int* ns, int count, const int* Ltab, std::vector<BatchIte
       items.push_back(it);
     }
     mcount[k] = (int)items.size() - mfirst[k];
+  }
+}
+
+// Most work items one plan holds (1.5 GiB of item list, 2 GiB of partials).
+constexpr uint64_t kMaxItems = 1ull << 26;
+
+// Chunk lengths for one batch: the tuned lengths, doubled for the order that
+// contributes the most items until the batch has at most
+// max(kMaxItems, count) items, so the item list and its partials stay bounded
+// and item indices fit in an int however large the batch.
+void plan_lengths(const int* ns, int count, const int* Ltune, int* Leff) {
+  uint64_t cnt[kBatchNMax + 1] = {0};
+  for (int k = 0; k < count; ++k) ++cnt[ns[k]];
+  for (int n = 0; n <= kBatchNMax; ++n) Leff[n] = Ltune[n] ? Ltune[n] : default_L(n < 1 ? 1 : n);
+  const uint64_t cap = std::max<uint64_t>(kMaxItems, (uint64_t)count);
+  for (;;) {
+    uint64_t total = 0, worst = 0;
+    int wn = -1;
+    for (int n = 1; n <= kBatchNMax; ++n) {
+      if (!cnt[n]) continue;
+      const uint64_t per_item = 32ull * (uint64_t)Leff[n];
+      const uint64_t each = ((1ull << (n - 1)) + per_item - 1) / per_item;
+      const uint64_t t = cnt[n] * each;
+      total += t;
+      if (each > 1 && t > worst) worst = t, wn = n;
+    }
+    if (total <= cap || wn < 0) break;
+    Leff[wn] *= 2;
   }
 }
 
@@ -441,6 +476,7 @@ int perm_batch_autotune(int n_lo, int n_hi) {
     return PERM_ECUDA;
   }
   if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return PERM_ECUDA;
+  ensure_kernels_loaded();
   std::lock_guard<std::mutex> lk(g_batch_mu);
   for (int n = n_lo; n <= n_hi; ++n) {
     tune_of(dev).L[n] = 0;
@@ -462,6 +498,7 @@ static int batch_run(const double* const* ptrs, const int* ns, int count, double
     return PERM_ECUDA;
   }
   if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return PERM_ECUDA;
+  ensure_kernels_loaded();
   cudaStream_t s = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(g_batch_mu);
   int* status = batch_status_word(dev);
@@ -509,7 +546,10 @@ static int batch_run(const double* const* ptrs, const int* ns, int count, double
     np->Ls.assign(tune_of(dev).L, tune_of(dev).L + kBatchNMax + 1);
     std::vector<BatchItem> items;
     std::vector<int> mf, mc;
-    build_items(ns, count, tune_of(dev).L, items, mf, mc);
+    int Leff[kBatchNMax + 1];
+    plan_lengths(ns, count, tune_of(dev).L, Leff);
+    build_items(ns, count, Leff, items, mf, mc);
+    if (items.size() > (size_t)std::max<uint64_t>(kMaxItems, (uint64_t)count)) return PERM_ENOMEM;
     np->nitems = (int)items.size();
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&np->items.p, items.size() * sizeof(BatchItem));

@@ -31,6 +31,8 @@ __global__ void k_mod_finalize(const uint64_t* __restrict__ partials, int nparts
   residues[q] = mont_mul(s, sr[q], p, c.pinv[q]);
 }
 
+void preload_mod_kernels() { load_kernel(k_mod_finalize); }
+
 }  // namespace perm
 
 namespace {
@@ -64,6 +66,7 @@ extern "C" int perm_mod01(const int8_t* A, int n, const uint64_t* primes, uint64
     return PERM_ECUDA;
   }
   if (cudaGetDevice(&dev) != cudaSuccess) return PERM_ECUDA;
+  ensure_kernels_loaded();
   cudaStream_t s = (cudaStream_t)stream;
 
   ModConsts c;

@@ -27,6 +27,8 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <cstdint>
 
 #include "dd.cuh"
@@ -405,7 +407,7 @@ struct WalkKernel {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    static int cached[64] = {0};
+    static std::atomic<int> cached[64];  // per device; filled once, read from any host thread
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (cached[dev] > 0) {
       resident = cached[dev];

@@ -25,6 +25,8 @@ __global__ void __launch_bounds__(kProbeThreads) k_dfma_probe(double* sink, int 
   sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+void preload_peak_kernels() { load_kernel(k_dfma_probe); }
+
 cudaError_t dfma_probe_launch(double* sink, int blocks, int iters, cudaStream_t stream) {
   k_dfma_probe<<<blocks, kProbeThreads, 0, stream>>>(sink, iters, 0.999999, 1e-7);
   return cudaGetLastError();

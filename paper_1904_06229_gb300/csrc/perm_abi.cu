@@ -6,6 +6,7 @@
 // CUDA kernels of this library.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <chrono>
 #include <cstdint>
 #include <cstdlib>
@@ -67,17 +68,23 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const double* __restri
   }
 }
 
+void preload_abi_kernels() { load_kernel(k_finalize); }
+
 cudaError_t finalize_launch(const double* partials, int nparts, bool cplx, int n, int mode, double* out,
                             cudaStream_t stream) {
   k_finalize<<<1, kFinThreads, 0, stream>>>(partials, nparts, cplx ? 1 : 0, n, mode, out);
   return cudaGetLastError();
 }
 
+namespace {
+std::mutex g_status_mu;
+int* g_status_words[64] = {nullptr};
+}  // namespace
+
 int device_status_word(int dev, int** out) {
-  static std::mutex mu;
-  static int* words[64] = {nullptr};
+  int** words = g_status_words;
   if (dev < 0 || dev >= 64) return -3;
-  std::lock_guard<std::mutex> lk(mu);
+  std::lock_guard<std::mutex> lk(g_status_mu);
   if (!words[dev]) {
     int* p = nullptr;
     cudaError_t e = cudaMalloc(&p, sizeof(int));
@@ -91,6 +98,42 @@ int device_status_word(int dev, int** out) {
   }
   *out = words[dev];
   return 0;
+}
+
+void ensure_kernels_loaded() {
+  static std::mutex mu;
+  static std::atomic<bool> done[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return;
+  }
+  if (done[dev].load(std::memory_order_acquire)) return;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev].load(std::memory_order_relaxed)) return;
+  for (int n = 1; n <= PERM_NMAX; ++n) {
+    for (int c = 0; c < 2; ++c)
+      for (int m = 0; m < 2; ++m)
+        for (int r = 0; r < 3; ++r)
+          walk_resident_blocks(n, c != 0, m ? kProdF32 : kProdF64, (RowMode)r);  // loads the walk kernel
+    if (n <= 32)
+      mod_resident_lo(n);
+    else if (n <= 48)
+      mod_resident_mid(n);
+    else
+      mod_resident_hi(n);
+  }
+  batch_resident_blocks_rows(kRowsF64);
+  batch_resident_blocks_rows(kRowsFixed);
+  preload_abi_kernels();
+  preload_batch_kernels();
+  preload_mod_kernels();
+  preload_peak_kernels();
+  preload_ryser2_kernels();
+  preload_sparse_kernels();
+  preload_band_kernels();
+  cudaGetLastError();
+  done[dev].store(true, std::memory_order_release);
 }
 
 RowMode rows_from_env() {
@@ -206,6 +249,7 @@ int run_walk(bool cplx, ProductMode pm, const double* A, int n, uint64_t first, 
   int dev = 0;
   int rc = current_device(&dev);
   if (rc) return rc;
+  ensure_kernels_loaded();
   int* status = nullptr;
   rc = device_status_word(dev, &status);
   if (rc) return rc;
@@ -344,7 +388,12 @@ void perm_shutdown(void) {
   int cur = -1, ndev = 0;
   cudaGetDevice(&cur);
   if (cudaGetDeviceCount(&ndev) == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(g_status_mu);
     for (int d = 0; d < ndev && d < kMaxDevices; ++d) {
+      if (g_status_words[d] && cudaSetDevice(d) == cudaSuccess) {
+        cudaFree(g_status_words[d]);
+        g_status_words[d] = nullptr;
+      }
       cudaMemPool_t pool;
       if (cudaDeviceGetDefaultMemPool(&pool, d) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
     }

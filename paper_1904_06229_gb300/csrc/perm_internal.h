@@ -113,6 +113,7 @@ cudaError_t batch_launch(const double* const* ptrs, const BatchItem* items, int 
                          const int* nmat_items, int count, double* item_partials, unsigned int* ticket,
                          double* out, int grid, int* status, cudaStream_t stream);
 int batch_resident_blocks();
+int batch_resident_blocks_rows(RowMode rows);
 
 // Per-device status word (device int, OR-ed by kernels; read and cleared by
 // perm_last_status).  Allocated on first use.
@@ -123,5 +124,28 @@ void batch_release_plans();
 
 // ---- peak probe ----
 cudaError_t dfma_probe_launch(double* sink, int blocks, int iters, cudaStream_t stream);
+
+// ---- kernel loading ----
+// CUDA loads kernels lazily by default, and loading a kernel waits until the
+// device is idle: a kernel first launched behind running work would make that
+// call block the host until the work is done.  Every entry point therefore
+// loads all of the library's kernels on the current device once, before its
+// first launch there (a few tens of milliseconds, once per device and process).
+template <typename T>
+inline void load_kernel(T* k) {
+  cudaFuncAttributes a;
+  cudaFuncGetAttributes(&a, k);
+}
+void preload_abi_kernels();     // perm_abi.cu: the fixed-order finalize
+void preload_batch_kernels();   // batch.cu: batch finalize and statistics
+void preload_mod_kernels();     // glynn_mod.cu: modular finalize
+void preload_peak_kernels();    // peak.cu: FP64 probe
+void preload_ryser2_kernels();  // ryser2.cu
+void preload_sparse_kernels();  // sparse.cu
+void preload_band_kernels();    // band.cu
+// Load every kernel on the current device (first call per device only; best
+// effort: a kernel that fails to load here fails again at its launch, where
+// the error is reported).
+void ensure_kernels_loaded();
 
 }  // namespace perm

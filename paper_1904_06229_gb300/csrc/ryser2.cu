@@ -263,6 +263,16 @@ cudaError_t r2_dispatch(int n, const double* C, const R2Params& p, int nbin, uin
   }
 }
 
+template <int LO, int HI>
+void r2_preload() {
+  if constexpr (LO <= HI) {
+    load_kernel(k_ryser2<LO>);
+    r2_preload<LO + 1, HI>();
+  }
+}
+
+void preload_ryser2_kernels() { r2_preload<1, PERM_NMAX>(); }
+
 }  // namespace perm
 
 namespace {
@@ -303,6 +313,7 @@ extern "C" int perm_c128_repeated(const double* C, const int* mult, int R, int n
     return PERM_ECUDA;
   }
   if (cudaGetDevice(&dev) != cudaSuccess) return PERM_ECUDA;
+  ensure_kernels_loaded();
   int* status = nullptr;
   if (device_status_word(dev, &status) != 0) return PERM_ECUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

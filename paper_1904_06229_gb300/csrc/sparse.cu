@@ -221,6 +221,16 @@ cudaError_t sp_dispatch(int n, const double* A, const SpParams& p, uint64_t tota
   }
 }
 
+template <int LO, int HI>
+void sp_preload() {
+  if constexpr (LO <= HI) {
+    load_kernel(k_sparse<LO>);
+    sp_preload<LO + 1, HI>();
+  }
+}
+
+void preload_sparse_kernels() { sp_preload<1, PERM_NMAX>(); }
+
 }  // namespace perm
 
 namespace {
@@ -330,6 +340,7 @@ int perm_c128_sparse(const double* A, int n, double* out, void* stream) {
     return PERM_ECUDA;
   }
   if (cudaGetDevice(&dev) != cudaSuccess) return PERM_ECUDA;
+  ensure_kernels_loaded();
   int* status = nullptr;
   if (device_status_word(dev, &status) != 0) return PERM_ECUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -1,7 +1,10 @@
 """Runtime behaviour on the GPU: checkpointed long runs through the range
 API, the host-side wait limit of perm_last_status (no GPU fault involved: a
-long but finite launch is simply waited on with a short limit), and a range
-split across two streams."""
+long but finite launch is simply waited on with a short limit), a range
+split across two streams, reuse after perm_shutdown, and first calls that
+return before their work is done."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -53,3 +56,56 @@ def test_two_streams_split_one_sum():
     full = P.perm_c128(A).cpu().numpy()
     ref = complex(full[0], full[1])
     assert abs(split - ref) <= 1e-12 * abs(ref)
+
+
+def test_shutdown_then_reuse():
+    """perm_shutdown frees the per-device status words, cached batch graphs and
+    the pool reserve; later calls allocate afresh and give the same results,
+    and a non-finite input is still reported afterwards."""
+    A = torch.from_numpy(W.complex_gaussian(12, 5)).cuda()
+    before = P.perm_c128(A).cpu()
+    mats = [torch.from_numpy(W.complex_gaussian(n, 40 + n)).cuda() for n in (8, 11, 13)]
+    b_before = P.perm_batch(mats).cpu()
+    torch.cuda.synchronize()
+    P.perm_shutdown()
+    P.perm_shutdown()  # twice is fine
+    assert torch.equal(P.perm_c128(A).cpu(), before)
+    assert torch.equal(P.perm_batch(mats).cpu(), b_before)
+    assert P.perm_last_status() == 0
+    bad = A.clone()
+    bad[3, 4] = complex(float("nan"), 0.0)
+    P.perm_c128(bad)
+    assert P.STATUS[P.perm_last_status()] == "PERM_ENONFINITE"
+    assert P.perm_last_status() == 0
+
+
+def test_first_calls_return_before_the_work_finishes():
+    """Compute calls are asynchronous, the first ones in a process included.
+    CUDA loads kernels lazily and a load waits for the device to go idle, so
+    the library loads all of its kernels when it first meets a device; a
+    second call made while the first one's walk is still running (here a
+    modular walk behind an n = 35 FP64 walk of about 4 s) must not wait for
+    it."""
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = (
+        "import time, torch\n"
+        "from paper_1904_06229_gb300 import perm as P, workloads as W\n"
+        "A = torch.from_numpy(W.complex_gaussian(35, 7)).cuda()\n"
+        "B = torch.from_numpy(W.zero_one(24, 6)).cuda()\n"
+        "pr = P.perm_default_primes()\n"
+        "torch.cuda.synchronize()\n"
+        "t0 = time.perf_counter(); P.perm_c128(A); t1 = time.perf_counter()\n"
+        "P.perm_mod01(B, pr); t2 = time.perf_counter()\n"
+        "torch.cuda.synchronize(); t3 = time.perf_counter()\n"
+        "print(t1 - t0, t2 - t1, t3 - t0)\n"
+    )
+    r = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True, cwd=root, timeout=900)
+    assert r.returncode == 0, r.stderr[-2000:]
+    first, second, total = map(float, r.stdout.split()[-3:])
+    print(f"first call {first:.3f} s, second call {second:.3f} s, all work {total:.3f} s")
+    assert total > 2.0
+    assert second < 0.25 * total
+    assert first + second < 0.5 * total
