@@ -11,13 +11,16 @@
 // Accuracy: a double-float addition or multiplication is accurate to about
 // 2^-47 relative, so the row sums drift by about sqrt(steps) 2^-48; every run
 // of 128 codes re-seeds them from exact int64 fixed-point row sums (the same
-// quantisation as the fixed-point walk), and the partial products are
-// renormalised by powers of two every 8 factors so they never leave the FP32
-// range.  Terms are rebuilt as doubles with integer bit operations and summed
-// like the other walks (FP64 run sums folded into double-double).
+// quantisation as the fixed-point walk), and the partial products (four
+// interleaved chains) are renormalised by powers of two every 8 factors so
+// they never leave the FP32 range.  Terms are rebuilt as doubles with integer
+// bit operations and summed like the other walks (FP64 run sums folded into
+// double-double).
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <atomic>
 
 #include <cstdint>
 
@@ -47,7 +50,10 @@ __device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, f
   l = __fsub_rn(e, __fsub_rn(h, s));
 }
 
-// a*b - c*d for double-floats, result renormalised.
+// a*b - c*d for double-floats.  The result is left as TwoSum's (s, e) plus
+// the products' low parts: |l| stays within a few units of the last place of
+// h, which the next product's FMAs take as it is (the pair is renormalised
+// only where it is stored: in the row sums, by df_add).
 __device__ __forceinline__ void df_mul_sub(float ah, float al, float bh, float bl, float ch, float cl, float dh,
                                            float dl, float& h, float& l) {
   const float p1 = __fmul_rn(ah, bh);
@@ -60,9 +66,8 @@ __device__ __forceinline__ void df_mul_sub(float ah, float al, float bh, float b
   e2 = __fmaf_rn(cl, dh, e2);
   float s, e;
   f_two_sum(p1, -p2, s, e);
-  e = __fadd_rn(e, __fsub_rn(e1, e2));
-  h = __fadd_rn(s, e);
-  l = __fsub_rn(e, __fsub_rn(h, s));
+  h = s;
+  l = __fadd_rn(e, __fsub_rn(e1, e2));
 }
 
 // a*b + c*d for double-floats, result renormalised.
@@ -104,34 +109,33 @@ __device__ __forceinline__ void split_double(double d, float& h, float& l) {
   l = __double2float_rn(d - (double)h);
 }
 
+// Product of the N row sums in four interleaved chains (rows i = c mod 4),
+// each renormalised by a power of two every 8 factors, then combined.
 template <int N>
 __device__ __forceinline__ void df_product(const cdf (&u)[N], double& pr, double& pi) {
-  cdf a = u[0];
-  int Ea = 0;
-  if constexpr (N == 1) {
-    cdf_renorm(a, Ea);
-    pr = f32_times_pow2(a.rh, Ea) + f32_times_pow2(a.rl, Ea);
-    pi = f32_times_pow2(a.ih, Ea) + f32_times_pow2(a.il, Ea);
-  } else {
-    cdf b = u[1];
-    int Eb = 0;
+  constexpr int NC = N < 4 ? N : 4;
+  cdf p[NC];
+  int E[NC];
 #pragma unroll
-    for (int i = 2; i < N; ++i) {
-      if (i & 1) {
-        b = cdf_mul(b, u[i]);
-        if ((i & 15) == 15) cdf_renorm(b, Eb);
-      } else {
-        a = cdf_mul(a, u[i]);
-        if ((i & 15) == 14) cdf_renorm(a, Ea);
-      }
-    }
-    cdf_renorm(a, Ea);
-    cdf_renorm(b, Eb);
-    a = cdf_mul(a, b);
-    const int E = Ea + Eb;
-    pr = f32_times_pow2(a.rh, E) + f32_times_pow2(a.rl, E);
-    pi = f32_times_pow2(a.ih, E) + f32_times_pow2(a.il, E);
+  for (int c = 0; c < NC; ++c) p[c] = u[c], E[c] = 0;
+#pragma unroll
+  for (int i = NC; i < N; ++i) {
+    const int c = i % NC;
+    p[c] = cdf_mul(p[c], u[i]);
+    if ((i / NC) % 8 == 7) cdf_renorm(p[c], E[c]);
   }
+  int Et = 0;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) cdf_renorm(p[c], E[c]), Et += E[c];
+  if constexpr (NC >= 2) p[0] = cdf_mul(p[0], p[1]);
+  if constexpr (NC >= 4) {
+    p[2] = cdf_mul(p[2], p[3]);
+    p[0] = cdf_mul(p[0], p[2]);
+  } else if constexpr (NC == 3) {
+    p[0] = cdf_mul(p[0], p[2]);
+  }
+  pr = f32_times_pow2(p[0].rh, Et) + f32_times_pow2(p[0].rl, Et);
+  pi = f32_times_pow2(p[0].ih, Et) + f32_times_pow2(p[0].il, Et);
 }
 
 template <int N>
@@ -272,7 +276,7 @@ struct DfKernel {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    static int cached[64] = {0};
+    static std::atomic<int> cached[64];  // per device; filled once, read from any host thread
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (cached[dev] > 0) {
       resident = cached[dev];
