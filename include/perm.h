@@ -145,7 +145,8 @@ int perm_c128_repeated(const double* C, const int* mult, int R, int n, double* o
  * A: `count` complex n x n matrices, contiguous (count * 2*n*n doubles,
  *    row-major interleaved), device or host; only entries with |i - j| <= k
  *    are read (the others are taken as zero).
- * n: 1..65535; k: 0..5; count >= 1.  out: 2*count doubles (re, im), device
+ * n: 1..65535; k: 0..5; 1 <= count <= 2^30, count * n * n <= 2^44
+ * (PERM_EINVAL otherwise).  out: 2*count doubles (re, im), device
  * or host.  One CTA per matrix; the window polynomial (2^(2k+1) complex
  * coefficients) lives in shared memory; coefficients are formed in a fixed
  * order (deterministic). */

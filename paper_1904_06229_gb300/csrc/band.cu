@@ -180,6 +180,9 @@ bool device_ptr_band(const void* p) {
 extern "C" int perm_c128_band(const double* A, int n, int k, int count, double* out, void* stream) {
   using namespace perm;
   if (n < 1 || n > 65535 || k < 0 || k > kBandKMax || count < 1 || count > (1 << 30)) return PERM_EINVAL;
+  // count * n * n complex entries must be addressable: at most 2^44 (256 TiB),
+  // far beyond any device, so the byte counts below cannot wrap
+  if ((double)count * (double)n * (double)n > 17592186044416.0) return PERM_EINVAL;
   if (!A || !out) return PERM_ENULL;
   int ndev = 0, dev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {

@@ -98,6 +98,11 @@ def test_argument_errors_before_device(lib):
     assert lib.perm_mod01(a, 3, ctypes.addressof(pr), a, None) == -7
     pr = (ctypes.c_uint64 * 4)(7, 11, 13, 16)
     assert lib.perm_mod01(a, 3, ctypes.addressof(pr), a, None) == -7
+    # band: sizes whose byte count would not be addressable
+    assert lib.perm_c128_band(a, 65535, 2, 1 << 30, a, None) == -1
+    assert lib.perm_c128_band(a, 65535, 2, 4097, a, None) == -1
+    assert lib.perm_c128_band(a, 10, 6, 1, a, None) == -1
+    assert lib.perm_c128_band(a, 10, 2, 0, a, None) == -1
 
 
 def test_no_cpu_fallback_without_device(lib):
