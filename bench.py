@@ -272,11 +272,16 @@ def run_gpu(args):
     ops_per_term = 6 * n - 4     # algorithmic FP64 pipe ops: 4(n-1) product + 2n row update
     flops_per_term = 8 * n - 6   # complex multiply = 6 flops, complex add = 2
     # FP64 instructions the kernel actually issues per code: with fixed-point
-    # rows the 2n row updates run on the integer pipes
-    issued = {"fixed": 4 * (n - 1) + 2, "fp64": 6 * n - 2, "df": 8}[rows]
+    # rows the 2n row updates run on the integer pipes, and the first n/2
+    # factors (kIxRows in glynn_walk_fx.cuh) are multiplied in integer block
+    # floating point, which joins the FP64 chains as one complex factor
+    k_ix = n // 2 if n >= 8 else 0
+    fixed_issued = 4 * (n - k_ix) + 4 if k_ix else 4 * (n - 1) + 2
+    issued = {"fixed": fixed_issued, "fp64": 6 * n - 2, "df": 8}[rows]
     avg_launch = sum(launch_s) / len(launch_s)
     achieved = CODES_PER_STEP * ops_per_term / avg_launch / 1e9
-    kname = {"fixed": f"perm::k_walk_fx<{n}, complex, FP64 product> (int64 fixed-point rows)",
+    kname = {"fixed": f"perm::k_walk_fx<{n}, complex, FP64 product> (int64 fixed-point rows; {k_ix} of the "
+                      f"factors in 64-bit integer block floating point)",
              "fp64": f"perm::k_walk<{n}, complex, FP64 product> (FP64 rows)",
              "df": f"perm::k_walk_df<{n}> (double-float rows and products, FP32 pipe)"}[rows]
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
@@ -289,8 +294,9 @@ def run_gpu(args):
                 "peak_source": "measured this run: perm_fp64_peak() DFMA probe (MEASURED_PEAKS.json has no FP64 "
                                "figure)",
                 "note": "achieved counts the algorithmic 6n-4 FP64-pipe ops per code; with fixed-point rows the "
-                        "2n row-update adds run exactly on the integer pipes, so frac can exceed 1 while the FP64 "
-                        "pipe itself runs at fp64_pipe_frac"}
+                        "2n row-update adds run exactly on the integer pipes and half of the product's factors are "
+                        "multiplied in 64-bit integer block floating point, so frac exceeds 1 while the FP64 pipe "
+                        "itself runs at fp64_pipe_frac"}
     line = {"metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -314,7 +320,7 @@ def run_gpu(args):
             a1.record(stream)
             torch.cuda.synchronize()
             at = a0.elapsed_time(a1) / 1e3
-            alt_issued = {"fixed": 4 * (n - 1) + 2, "fp64": 6 * n - 2, "df": 8}[alt]
+            alt_issued = {"fixed": fixed_issued, "fp64": 6 * n - 2, "df": 8}[alt]
             o, rp = out.cpu().numpy(), ref_part.cpu().numpy()
             va, vr_ = complex(o[0] + o[1], o[2] + o[3]), complex(rp[0] + rp[1], rp[2] + rp[3])
             line["alt_rows"].append({"rows": alt, "terms_per_s": CODES_PER_STEP / at,

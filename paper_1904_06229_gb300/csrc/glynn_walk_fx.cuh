@@ -89,27 +89,124 @@ __device__ __forceinline__ float fx_to_f32(long long v, int lzref) {
 template <int N, bool CPLX, int MODE, bool RN = false>
 struct FxProduct;
 
-// FP64 product of w_i = v_i 2^(eb_i - 1086), two interleaved chains.
+// ---- integer block floating point for part of the complex product ----
+// The FP64 pipe bounds the walk (four DFMAs per factor) while the integer
+// pipes have room, so the product of the first kIxRows<N> row sums is formed
+// from their exact int64 values in 64-bit integer block floating point: a
+// complex number (X + iY) 2^e with int64 X, Y and max(|X|, |Y|) brought to
+// [2^61, 2^62] by a left shift; each factor is shifted into the same range,
+// the complex product takes the signed high halves of four 64 x 64-bit
+// products (truncated, so each step errs by under 2^-57 of the result, finer
+// than FP64 rounding), and the result is renormalised.  The block enters the
+// FP64 chains once per term as one complex double.
+template <int N>
+constexpr int kIxRows = N >= 8 ? N / 2 : 0;
+
+__device__ __forceinline__ int ix_shift(long long x, long long y) {
+  const unsigned long long m = (unsigned long long)(x ^ (x >> 63)) | (unsigned long long)(y ^ (y >> 63));
+  return max(__clzll((long long)m) - 2, 0);
+}
+
+__device__ __forceinline__ long long ix_shl(long long x, int k) { return (long long)((unsigned long long)x << k); }
+
+// One step of a block: (X + iY) 2^e times (a + ib) 2^f, both normalised.
+__device__ __forceinline__ void ix_mul(long long& X, long long& Y, int& e, long long a, long long b, int f) {
+  const long long re = __mul64hi(X, a) - __mul64hi(Y, b);
+  const long long im = __mul64hi(X, b) + __mul64hi(Y, a);
+  const int kz = ix_shift(re, im);
+  X = ix_shl(re, kz);
+  Y = ix_shl(im, kz);
+  e += f + 64 - kz;
+}
+
+// (X + iY) 2^e = prod_{i < K} (vr_i + i vi_i) (e relative to the rows' scales),
+// in two interleaved blocks (even and odd rows) joined at the end, so that
+// two independent dependency chains are in flight.
+template <int N, int K>
+__device__ __forceinline__ void ix_product(const long long (&vr)[N], const long long (&vi)[N], long long& X,
+                                           long long& Y, int& e) {
+  const int k0 = ix_shift(vr[0], vi[0]);
+  X = ix_shl(vr[0], k0);
+  Y = ix_shl(vi[0], k0);
+  e = -k0;
+  if constexpr (K == 1) return;
+  const int k1 = ix_shift(vr[1], vi[1]);
+  long long U = ix_shl(vr[1], k1), V = ix_shl(vi[1], k1);
+  int g = -k1;
+#pragma unroll
+  for (int i = 2; i < K; ++i) {
+    const int kf = ix_shift(vr[i], vi[i]);
+    const long long a = ix_shl(vr[i], kf), b = ix_shl(vi[i], kf);
+    if (i & 1)
+      ix_mul(U, V, g, a, b, -kf);
+    else
+      ix_mul(X, Y, e, a, b, -kf);
+  }
+  ix_mul(X, Y, e, U, V, g);
+}
+
+// Exponent offset of the integer block: sum over its rows of (eb_i - 1086).
+template <int N>
+__device__ __forceinline__ int ix_offset(const int* sEb) {
+  int c = 0;
+#pragma unroll 1
+  for (int i = 0; i < kIxRows<N>; ++i) c += sEb[i] - 1086;
+  return c;
+}
+
+// FP64 product of w_i = v_i 2^(eb_i - 1086), two interleaved chains; with
+// RN = false the first kIxRows<N> factors come from the integer block.
 template <int N, bool RN>
 struct FxProduct<N, true, kProdF64, RN> {
+  static constexpr int K = RN ? 0 : kIxRows<N>;
+
   static __device__ __forceinline__ void eval(const long long (&vr)[N], const long long (&vi)[N], const int* sEb,
                                               double& pr, double& pi, double z) {
-    double ar = fx_to_double<RN>(vr[0], sEb[0]), ai = fx_to_double<RN>(vi[0], sEb[0]);
-    if constexpr (N == 1) {
-      pr = ar;
-      pi = ai;
-    } else {
-      double br = fx_to_double<RN>(vr[1], sEb[1]), bi = fx_to_double<RN>(vi[1], sEb[1]);
+    eval(vr, vi, sEb, pr, pi, z, K > 0 ? ix_offset<N>(sEb) : 0);
+  }
+
+  // ixc: ix_offset<N>(sEb), computed once by the caller
+  static __device__ __forceinline__ void eval(const long long (&vr)[N], const long long (&vi)[N], const int* sEb,
+                                              double& pr, double& pi, double z, int ixc) {
+    if constexpr (K == 0) {
+      double ar = fx_to_double<RN>(vr[0], sEb[0]), ai = fx_to_double<RN>(vi[0], sEb[0]);
+      if constexpr (N == 1) {
+        pr = ar;
+        pi = ai;
+      } else {
+        double br = fx_to_double<RN>(vr[1], sEb[1]), bi = fx_to_double<RN>(vi[1], sEb[1]);
 #pragma unroll
-      for (int i = 2; i < N; ++i) {
+        for (int i = 2; i < N; ++i) {
+          const int eb = sEb[i];
+          const double cr = fx_to_double<RN>(vr[i], eb), ci = fx_to_double<RN>(vi[i], eb);
+          if (i & 1)
+            cmul(br, bi, cr, ci, z);
+          else
+            cmul(ar, ai, cr, ci, z);
+        }
+        cmul(ar, ai, br, bi, z);
+        pr = ar;
+        pi = ai;
+      }
+    } else {
+      static_assert(N - K >= 2, "the FP64 part keeps two chains");
+      long long X, Y;
+      int e;
+      ix_product<N, K>(vr, vi, X, Y, e);
+      double ar = fx_to_double<RN>(vr[K], sEb[K]), ai = fx_to_double<RN>(vi[K], sEb[K]);
+      double br = fx_to_double<RN>(vr[K + 1], sEb[K + 1]), bi = fx_to_double<RN>(vi[K + 1], sEb[K + 1]);
+#pragma unroll
+      for (int i = K + 2; i < N; ++i) {
         const int eb = sEb[i];
         const double cr = fx_to_double<RN>(vr[i], eb), ci = fx_to_double<RN>(vi[i], eb);
-        if (i & 1)
+        if ((i - K) & 1)
           cmul(br, bi, cr, ci, z);
         else
           cmul(ar, ai, cr, ci, z);
       }
       cmul(ar, ai, br, bi, z);
+      const int et = e + ixc;
+      cmul(ar, ai, scalbn((double)X, et), scalbn((double)Y, et), z);
       pr = ar;
       pi = ai;
     }
@@ -140,6 +237,10 @@ struct FxProduct<N, false, kProdF64, RN> {
 // FP32 significands straight from the integers; exponents add in integers.
 template <int N, bool RN>
 struct FxProduct<N, true, kProdF32, RN> {
+  static __device__ __forceinline__ void eval(const long long (&vr)[N], const long long (&vi)[N], const int* sEb,
+                                              double& pr, double& pi, double z, int) {
+    eval(vr, vi, sEb, pr, pi, z);
+  }
   static __device__ __forceinline__ void eval(const long long (&vr)[N], const long long (&vi)[N], const int* sEb,
                                               double& pr, double& pi, double) {
     float ar = 1.f, ai = 0.f, br = 1.f, bi = 0.f;
@@ -258,6 +359,7 @@ __device__ __forceinline__ void thread_walk_c128_fx(const longlong2* __restrict_
                                                     uint64_t r, const uint64_t end, dd& accr, dd& acci) {
   if (r >= end) return;
   const double z = fx_to_double(sV0[0].x, sEb[0]) * 0.0;  // a register zero (+-0.0) for the product FMAs
+  const int ixc = MODE == kProdF64 ? ix_offset<N>(sEb) : 0;
   long long vr[N], vi[N];
   {
     // seed once (App. A steps 2, 5-8, in v = 2w form): exact, never redone
@@ -288,7 +390,7 @@ __device__ __forceinline__ void thread_walk_c128_fx(const longlong2* __restrict_
     uint32_t odd = (uint32_t)(r & 1ull);
     for (; r < run_end; ++r) {
       double pr, pi;
-      FxProduct<N, true, MODE>::eval(vr, vi, sEb, pr, pi, z);
+      FxProduct<N, true, MODE>::eval(vr, vi, sEb, pr, pi, z, ixc);
       const double sg = pm_one(odd);
       odd ^= 1u;
       sr = fma(sg, pr, sr);

@@ -163,12 +163,13 @@ __global__ void __launch_bounds__(kWalkThreads) k_ryser2(const double* __restric
 #pragma unroll 1
     for (int k = 1; k < R; ++k) wrest *= sBin[prm.bin_off[k] + g[k]], par += g[k];
     uint32_t odd = (uint32_t)(par & 1);
+    const int ixc = ix_offset<N>(sEb);
     while (r < end) {
       const uint64_t run_end = min(end, r + kRun);
       double sr = 0.0, si = 0.0;
       for (; r < run_end; ++r) {
         double pr, pi;
-        FxProduct<N, true, kProdF64>::eval(vr, vi, sEb, pr, pi, z);
+        FxProduct<N, true, kProdF64>::eval(vr, vi, sEb, pr, pi, z, ixc);
         const double sw = flip_sign(fma(wrest, bin0[g0], z), odd);  // (-1)^{sum g} prod binom
         sr = fma(sw, pr, sr);
         si = fma(sw, pi, si);
