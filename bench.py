@@ -272,10 +272,11 @@ def run_gpu(args):
     ops_per_term = 6 * n - 4     # algorithmic FP64 pipe ops: 4(n-1) product + 2n row update
     flops_per_term = 8 * n - 6   # complex multiply = 6 flops, complex add = 2
     # FP64 instructions the kernel actually issues per code: with fixed-point
-    # rows the 2n row updates run on the integer pipes, and the first n/2
-    # factors (kIxRows in glynn_walk_fx.cuh) are multiplied in integer block
-    # floating point, which joins the FP64 chains as one complex factor
-    k_ix = n // 2 if n >= 8 else 0
+    # rows the 2n row updates run on the integer pipes, and the first
+    # min(17n/20, n - 2) factors (kIxRows in glynn_walk_fx.cuh) are multiplied
+    # in integer block floating point, which joins the FP64 chains as one
+    # complex factor
+    k_ix = min((n * 17) // 20, n - 2) if n >= 8 else 0
     fixed_issued = 4 * (n - k_ix) + 4 if k_ix else 4 * (n - 1) + 2
     issued = {"fixed": fixed_issued, "fp64": 6 * n - 2, "df": 8}[rows]
     avg_launch = sum(launch_s) / len(launch_s)
