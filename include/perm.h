@@ -57,8 +57,10 @@ typedef enum {
  * Row sums are held exactly as 64-bit fixed-point integers (each row scaled by
  * a power of two, 2^F_i with F_i = 61 - floor(log2 max(sum_j |Re a_ij|,
  * sum_j |Im a_ij|)), entries rounded to that grid once), so the Gray-step
- * updates are exact integer additions and never drift; each factor is turned
- * into a double by integer bit operations and the products are formed in FP64
+ * updates are exact integer additions and never drift.  For complex A the
+ * product of about 0.85 n of the row sums is formed from their integers in
+ * 64-bit integer block floating point (error per factor under 2^-56), the
+ * rest and the real case in FP64 from doubles built by integer bit operations
  * (fused multiply-adds).  Each thread's terms are summed in FP64 over runs of
  * at most 4096 codes and folded into a double-double accumulator; the per-
  * thread accumulators are combined with warp shuffles and a fixed-order tree
