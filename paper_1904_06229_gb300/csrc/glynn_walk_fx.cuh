@@ -172,11 +172,12 @@ __device__ __forceinline__ int ix_offset(const int* sEb) {
   return c;
 }
 
-// FP64 product of w_i = v_i 2^(eb_i - 1086), two interleaved chains; with
-// RN = false the first kIxRows<N> factors come from the integer block.
+// Product of w_i = v_i 2^(eb_i - 1086): the first kIxRows<N> factors from the
+// integer block, the others in FP64 (two interleaved chains; RN selects how
+// their doubles are rounded).
 template <int N, bool RN>
 struct FxProduct<N, true, kProdF64, RN> {
-  static constexpr int K = RN ? 0 : kIxRows<N>;
+  static constexpr int K = kIxRows<N>;
 
   static __device__ __forceinline__ void eval(const long long (&vr)[N], const long long (&vi)[N], const int* sEb,
                                               double& pr, double& pi, double z) {

@@ -15,8 +15,10 @@
 // in binary-reflected Gray order, so stepping a digit toggles one column and
 // wrapping a digit toggles one (T) or two (S_l) columns.  Row sums are exact
 // int64 fixed point (per-row power-of-two scale, as in the fixed-point Gray
-// walk), products FP64, and each signed term is added straight into
-// double-double accumulators (Ryser's un-halved sum cancels strongly).
+// walk), products as in that walk (integer block floating point for most
+// factors, FP64 with round-to-nearest conversions for the rest), and each
+// signed term is added straight into double-double accumulators (Ryser's
+// un-halved sum cancels strongly).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -138,9 +140,10 @@ __global__ void __launch_bounds__(kWalkThreads) k_sparse(const double* __restric
     }
     uint32_t odd = (uint32_t)(__popcll((long long)J) & 1);
     const int t0 = prm.size[0];
+    const int ixc = ix_offset<N>(sEb);
     for (; r < end; ++r) {
       double pr, pi;
-      FxProduct<N, true, kProdF64, true>::eval(vr, vi, sEb, pr, pi, z);
+      FxProduct<N, true, kProdF64, true>::eval(vr, vi, sEb, pr, pi, z, ixc);
       accr = dd_add_d(accr, flip_sign(pr, odd));  // (-1)^|J| prod_i s_i
       acci = dd_add_d(acci, flip_sign(pi, odd));
       if (r + 1 >= end) continue;
