@@ -145,7 +145,8 @@ def run_reference(args):
     t0 = time.perf_counter()
     O.glynn_partial_parts(A, 0, probe, parts=cores, threads=cores)
     rate = probe / max(time.perf_counter() - t0, 1e-4)
-    per_step = int(max(cores, min(1 << 30, rate * min(10.0, 150.0 / max(1, args.steps + args.warmup)))))
+    per_step = int(max(cores, min(1 << 30, rate * min(args.reference_step_seconds,
+                                                      150.0 / max(1, args.steps + args.warmup)))))
     for w in range(args.warmup):
         O.glynn_partial_parts(A, w * per_step, per_step, parts=cores, threads=cores)
     t0 = time.perf_counter()
@@ -570,6 +571,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--reference-step-seconds", type=float, default=10.0,
+                    help="host seconds per step of the reference arm (the CPU oracle)")
     ap.add_argument("--batch-sample", type=int, default=2000)
     ap.add_argument("--batch-study", type=int, default=0,
                     help="also run the whole batch study (e.g. 200000 matrices) in one launch; minutes")
