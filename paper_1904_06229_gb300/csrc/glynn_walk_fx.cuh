@@ -138,11 +138,13 @@ __device__ __forceinline__ void ix_mul(long long& X, long long& Y, int& e, long 
 }
 
 // (X + iY) 2^e = prod_{i < K} (vr_i + i vi_i) (e relative to the rows' scales),
-// in two interleaved blocks (even and odd rows) joined at the end, so that
-// two independent dependency chains are in flight.
+// in interleaved blocks joined at the end, so that independent dependency
+// chains are in flight: three for long blocks (K >= 24; measured 3 % faster
+// at n = 40), two for shorter ones (3 % faster at the batch study's orders).
 template <int N, int K>
 __device__ __forceinline__ void ix_product(const long long (&vr)[N], const long long (&vi)[N], long long& X,
                                            long long& Y, int& e) {
+  constexpr int C = K >= 24 ? 3 : 2;
   const int k0 = ix_shift(vr[0], vi[0]);
   X = ix_shl(vr[0], k0);
   Y = ix_shl(vi[0], k0);
@@ -151,14 +153,32 @@ __device__ __forceinline__ void ix_product(const long long (&vr)[N], const long 
   const int k1 = ix_shift(vr[1], vi[1]);
   long long U = ix_shl(vr[1], k1), V = ix_shl(vi[1], k1);
   int g = -k1;
+  if constexpr (C == 2) {
 #pragma unroll
-  for (int i = 2; i < K; ++i) {
-    const int kf = ix_shift(vr[i], vi[i]);
-    const long long a = ix_shl(vr[i], kf), b = ix_shl(vi[i], kf);
-    if (i & 1)
-      ix_mul(U, V, g, a, b, -kf);
-    else
-      ix_mul(X, Y, e, a, b, -kf);
+    for (int i = 2; i < K; ++i) {
+      const int kf = ix_shift(vr[i], vi[i]);
+      const long long a = ix_shl(vr[i], kf), b = ix_shl(vi[i], kf);
+      if (i & 1)
+        ix_mul(U, V, g, a, b, -kf);
+      else
+        ix_mul(X, Y, e, a, b, -kf);
+    }
+  } else {
+    const int k2 = ix_shift(vr[2], vi[2]);
+    long long P = ix_shl(vr[2], k2), Q = ix_shl(vi[2], k2);
+    int h = -k2;
+#pragma unroll
+    for (int i = 3; i < K; ++i) {
+      const int kf = ix_shift(vr[i], vi[i]);
+      const long long a = ix_shl(vr[i], kf), b = ix_shl(vi[i], kf);
+      if (i % 3 == 0)
+        ix_mul(X, Y, e, a, b, -kf);
+      else if (i % 3 == 1)
+        ix_mul(U, V, g, a, b, -kf);
+      else
+        ix_mul(P, Q, h, a, b, -kf);
+    }
+    ix_mul(U, V, g, P, Q, h);
   }
   ix_mul(X, Y, e, U, V, g);
 }
