@@ -1,0 +1,61 @@
+"""Edge cases of the complex product's integer block floating point (most
+factors of each term multiplied from the exact int64 row sums): exponent
+bookkeeping across rows of very different scale, row sums that are exactly
+zero at many codes, and integer matrices whose permanent is known exactly."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_1904_06229_gb300 import perm as P
+from paper_1904_06229_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-10
+U64 = 2.0 ** -53
+
+
+def gpu_c128(A):
+    t = torch.from_numpy(np.ascontiguousarray(np.asarray(A, dtype=np.complex128))).cuda()
+    r = P.perm_c128(t).cpu().numpy()
+    assert P.perm_last_status() == 0
+    return complex(r[0], r[1])
+
+
+@pytest.mark.parametrize("n", [10, 24, 30])
+def test_rows_of_very_different_scale(n):
+    """Row i scaled by 2^s_i with sum s_i = 0: per is unchanged, and since each
+    row's fixed-point scale absorbs its 2^s_i exactly, so is every term the
+    kernel forms; the result must be the same double, bit for bit."""
+    A = W.complex_gaussian(n, 900 + n)
+    rng = np.random.default_rng(n)
+    s = rng.integers(-30, 31, size=n)
+    s[-1] = -int(s[:-1].sum())
+    B = A * np.ldexp(1.0, s)[:, None]
+    assert gpu_c128(B) == gpu_c128(A)
+
+
+@pytest.mark.parametrize("n", [9, 16, 23])
+def test_integer_matrices_exact(n):
+    """+-1, 0-1 and all-ones matrices as complex128: many row sums are exactly
+    zero at many codes; the result equals the exact integer permanent."""
+    for A in (W.bernoulli_pm1(n, 40 + n), W.zero_one(n, 50 + n), np.ones((n, n), dtype=np.int8)):
+        ex = O.per_exact(A)
+        got = gpu_c128(A.astype(np.float64))
+        assert got.imag == 0.0
+        assert abs(got.real - ex) <= REL * abs(ex) if ex else got.real == 0.0
+
+
+@pytest.mark.parametrize("n", [12, 18])
+def test_complex_unit_entries(n):
+    """Entries in {1, -1, i, -i} against the long-double oracle and the
+    transpose."""
+    k = np.random.default_rng(70 + n).integers(0, 4, size=(n, n))
+    A = (1j) ** k
+    re, im, asum = O.per(A)
+    ref = complex(float(re), float(im))
+    got = gpu_c128(A)
+    tol = max(REL * abs(ref), 64 * n * U64 * float(asum))
+    assert abs(got - ref) <= tol
+    assert abs(gpu_c128(A.T) - ref) <= tol
