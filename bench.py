@@ -1,17 +1,25 @@
 """Benchmark: Gray-code Glynn permanent throughput on the n = 40 complex128
 Haar workload (S(1600, 40): sqrt(1600) times the top-left 40 x 40 block of a
-Haar unitary of order 1600), as terms/s and as a fraction of the measured
-FP64 pipe rate; the batched random-matrix study (perms/s, batched vs one
-launch per matrix) on a sample; the CPU oracle as baseline.
+Haar unitary of order 1600), as terms/s and against the measured FP64 DFMA
+rate; the batched random-matrix study (perms/s, batched vs one launch per
+matrix) on a sample; the CPU oracle as baseline.
 
 A step is one pass of the whole hot path (stage A, seed, Gray walk with
 product / signed accumulate / row update, double-double reduction) over one
-slice of 2^33 consecutive Gray codes of the n = 40 sum: 32 * 2^33 steps'
-worth of codes make up the whole permanent (2^39 codes), so step s covers
-slice (rank, s) of it.  Under torchrun each rank walks its own slices
-(weak scaling; the partials' exchange is a 32-byte host gather after timing).
+slice of 2^33 consecutive Gray codes of the n = 40 sum: 64 such slices make
+up the whole permanent (2^39 codes), and step s covers slice (rank, s) of
+it.  Under torchrun each rank walks its own slices (weak scaling; the
+partials' exchange is a 32-byte host gather after timing).
+
+Besides the contract's keys the JSON line carries: alt_rows (the FP64-row
+and double-float walks on the same slice), batch (a sample of the batch
+study, batched vs one launch per matrix), exact (0-1 permanents n = 30, 36),
+precision (FP32 products vs FP64), next_rows (repeated-column, sparse and
+band timings), stats (batch statistics), err_vs_oracle, and with
+--batch-study COUNT the whole batch study in one launch (batch_study).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--batch-sample M] [--batch-study COUNT]
 """
 from __future__ import annotations
 
