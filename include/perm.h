@@ -29,6 +29,15 @@
  *     combined in a fixed order, never with floating-point atomics.
  *   - The library never falls back to the CPU.  Without a CUDA device every
  *     compute call returns PERM_ECUDA.
+ *   - Every compute call opens an NVTX range named after itself (visible in
+ *     Nsight timelines; a no-op without a profiler).
+ *   - For testing callers' error handling, the environment variable
+ *     PERM_FAULT=plan|launch|finalize[:k] makes the walk entry points
+ *     (perm_c128, perm_f64, their _range and _f32p forms) fail at that step
+ *     -- plan: PERM_ENOMEM before any device work; launch: PERM_ECUDA before
+ *     the walk is launched; finalize: PERM_ECUDA after the walk, with no
+ *     result written -- on every call, or with ":k" only on the k-th call
+ *     that reaches the step.  No device fault is involved.
  */
 #ifndef PERM_H_
 #define PERM_H_

@@ -179,6 +179,7 @@ bool device_ptr_band(const void* p) {
 
 extern "C" int perm_c128_band(const double* A, int n, int k, int count, double* out, void* stream) {
   using namespace perm;
+  TraceRange trace("perm_c128_band");
   if (n < 1 || n > 65535 || k < 0 || k > kBandKMax || count < 1 || count > (1 << 30)) return PERM_EINVAL;
   // count * n * n complex entries must be addressable: at most 2^44 (256 TiB),
   // far beyond any device, so the byte counts below cannot wrap

@@ -469,6 +469,7 @@ int autotune_order(int dev, int n) {
 extern "C" {
 
 int perm_batch_autotune(int n_lo, int n_hi) {
+  TraceRange trace("perm_batch_autotune");
   if (n_lo < 1 || n_hi > kBatchNMax || n_lo > n_hi) return PERM_EINVAL;
   int count = 0, dev = 0;
   if (cudaGetDeviceCount(&count) != cudaSuccess || count < 1) {
@@ -595,10 +596,12 @@ static int batch_run(const double* const* ptrs, const int* ns, int count, double
 }
 
 int perm_batch(const double* const* ptrs, const int* ns, int count, double* out, void* stream) {
+  TraceRange trace("perm_batch");
   return batch_run(ptrs, ns, count, out, stream, nullptr);
 }
 
 int perm_batch_stats(const double* const* ptrs, const int* ns, int count, double* out, double* stats, void* stream) {
+  TraceRange trace("perm_batch_stats");
   if (!stats) return PERM_ENULL;
   const int* d_ns = nullptr;
   std::lock_guard<std::mutex> lk(g_stats_mu);

@@ -56,6 +56,7 @@ uint64_t pow_r_mod(uint64_t p, int k) {  // R^k mod p, R = 2^64
 
 extern "C" int perm_mod01(const int8_t* A, int n, const uint64_t* primes, uint64_t* residues, void* stream) {
   using namespace perm;
+  TraceRange trace("perm_mod01");
   if (n < 1 || n > PERM_NMAX) return PERM_EINVAL;
   if (!A || !primes || !residues) return PERM_ENULL;
   int rc = check_moduli(primes, 4);

@@ -12,7 +12,10 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <string>
 #include <thread>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "dd.cuh"
 #include "perm.h"
@@ -98,6 +101,29 @@ int device_status_word(int dev, int** out) {
   }
   *out = words[dev];
   return 0;
+}
+
+TraceRange::TraceRange(const char* name) { nvtxRangePushA(name); }
+TraceRange::~TraceRange() { nvtxRangePop(); }
+
+bool fault_injected(const char* stage) {
+  static std::mutex mu;
+  static std::string last;
+  static uint64_t calls = 0;
+  const char* e = std::getenv("PERM_FAULT");
+  if (!e || !*e) return false;
+  const std::string spec(e);
+  const size_t colon = spec.find(':');
+  const std::string name = spec.substr(0, colon);
+  if (name != stage) return false;
+  if (colon == std::string::npos) return true;
+  const uint64_t k = std::strtoull(spec.c_str() + colon + 1, nullptr, 10);
+  std::lock_guard<std::mutex> lk(mu);
+  if (spec != last) {
+    last = spec;
+    calls = 0;
+  }
+  return ++calls == k;
 }
 
 void ensure_kernels_loaded() {
@@ -246,6 +272,7 @@ int run_walk(bool cplx, ProductMode pm, const double* A, int n, uint64_t first, 
   if (!A || !out) return PERM_ENULL;
   const uint64_t total = 1ull << (n - 1);
   if (first > total || count > total - first) return PERM_EINVAL;
+  if (fault_injected("plan")) return PERM_ENOMEM;  // as if the scratch could not be had
   int dev = 0;
   int rc = current_device(&dev);
   if (rc) return rc;
@@ -286,6 +313,7 @@ int run_walk(bool cplx, ProductMode pm, const double* A, int n, uint64_t first, 
   double* partials = (double*)(scr.base + offP);
   double* dOut = o_dev ? out : (double*)(scr.base + offO);
 
+  if (fault_injected("launch")) return PERM_ECUDA;  // as if the walk's launch failed
   uint64_t done = 0;
   do {
     const uint64_t len = (count - done) < kCodesPerLaunch ? (count - done) : kCodesPerLaunch;
@@ -295,6 +323,7 @@ int run_walk(bool cplx, ProductMode pm, const double* A, int n, uint64_t first, 
     done += len;
   } while (done < count);
 
+  if (fault_injected("finalize")) return PERM_ECUDA;  // the walk ran; its result is not delivered
   cudaError_t e = finalize_launch(partials, blocks, cplx, n, final_mode, dOut, s);
   if (e != cudaSuccess) return status_of(e);
   if (!o_dev) {
@@ -309,29 +338,35 @@ int run_walk(bool cplx, ProductMode pm, const double* A, int n, uint64_t first, 
 extern "C" {
 
 int perm_c128(const double* A, int n, double* out, void* stream) {
+  TraceRange trace("perm_c128");
   if (n < 1 || n > PERM_NMAX) return PERM_EINVAL;
   return run_walk(true, kProdF64, A, n, 0, 1ull << (n - 1), 0, out, stream);
 }
 
 int perm_f64(const double* A, int n, double* out, void* stream) {
+  TraceRange trace("perm_f64");
   if (n < 1 || n > PERM_NMAX) return PERM_EINVAL;
   return run_walk(false, kProdF64, A, n, 0, 1ull << (n - 1), 0, out, stream);
 }
 
 int perm_c128_range(const double* A, int n, uint64_t first, uint64_t count, double* partial_dd, void* stream) {
+  TraceRange trace("perm_c128_range");
   return run_walk(true, kProdF64, A, n, first, count, 1, partial_dd, stream);
 }
 
 int perm_f64_range(const double* A, int n, uint64_t first, uint64_t count, double* partial_dd, void* stream) {
+  TraceRange trace("perm_f64_range");
   return run_walk(false, kProdF64, A, n, first, count, 1, partial_dd, stream);
 }
 
 int perm_c128_f32p(const double* A, int n, double* out, void* stream) {
+  TraceRange trace("perm_c128_f32p");
   if (n < 1 || n > PERM_NMAX) return PERM_EINVAL;
   return run_walk(true, kProdF32, A, n, 0, 1ull << (n - 1), 0, out, stream);
 }
 
 int perm_f64_f32p(const double* A, int n, double* out, void* stream) {
+  TraceRange trace("perm_f64_f32p");
   if (n < 1 || n > PERM_NMAX) return PERM_EINVAL;
   return run_walk(false, kProdF32, A, n, 0, 1ull << (n - 1), 0, out, stream);
 }

@@ -125,6 +125,23 @@ void batch_release_plans();
 // ---- peak probe ----
 cudaError_t dfma_probe_launch(double* sink, int blocks, int iters, cudaStream_t stream);
 
+// ---- tracing and host-side fault injection ----
+// NVTX range named after a C ABI entry point, open for the duration of the
+// host call (header-only NVTX: a no-op unless a profiler is attached).
+class TraceRange {
+ public:
+  explicit TraceRange(const char* name);
+  ~TraceRange();
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+// True when the environment variable PERM_FAULT names `stage` ("plan",
+// "launch" or "finalize"): "stage" fails every call that reaches the step,
+// "stage:k" only the k-th such call of the process (counted from the time
+// the variable took its current value).  The caller then returns the error
+// code the failing step would give, without touching the device.
+bool fault_injected(const char* stage);
+
 // ---- kernel loading ----
 // CUDA loads kernels lazily by default, and loading a kernel waits until the
 // device is idle: a kernel first launched behind running work would make that

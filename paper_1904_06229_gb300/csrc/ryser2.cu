@@ -290,6 +290,7 @@ bool device_ptr_r2(const void* p) {
 }  // namespace
 
 extern "C" int perm_c128_repeated(const double* C, const int* mult, int R, int n, double* out, void* stream) {
+  perm::TraceRange trace("perm_c128_repeated");
   using namespace perm;
   if (n < 1 || n > PERM_NMAX || R < 1 || R > n) return PERM_EINVAL;
   if (!C || !mult || !out) return PERM_ENULL;

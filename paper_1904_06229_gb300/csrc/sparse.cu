@@ -335,6 +335,7 @@ int perm_sparse_partition(const double* A_host, int n, int* block, uint64_t* cou
 
 int perm_c128_sparse(const double* A, int n, double* out, void* stream) {
   using namespace perm;
+  TraceRange trace("perm_c128_sparse");
   if (n < 1 || n > PERM_NMAX) return PERM_EINVAL;
   if (!A || !out) return PERM_ENULL;
   int ndev = 0, dev = 0;

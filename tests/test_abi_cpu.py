@@ -142,3 +142,22 @@ def test_sparse_partition_host(lib):
         assert count == O.partition_count(block)
         assert count <= O.partition_count(O.greedy_partition(A))
         assert math.log2(count) <= n
+
+
+def test_fault_injection_plan_stage(lib, monkeypatch):
+    """PERM_FAULT=plan makes a walk call fail as if its scratch could not be
+    had (PERM_ENOMEM), before any device work; "plan:k" fails only the k-th
+    call that reaches that step."""
+    buf = (ctypes.c_double * 8)(1, 0, 0, 0, 0, 0, 0, 0)
+    out = (ctypes.c_double * 4)()
+    a, o = ctypes.addressof(buf), ctypes.addressof(out)
+    monkeypatch.setenv("PERM_FAULT", "plan")
+    assert lib.perm_c128(a, 1, o, None) == -6
+    assert lib.perm_f64_range(a, 1, 0, 1, o, None) == -6
+    monkeypatch.setenv("PERM_FAULT", "plan:2")
+    codes = [lib.perm_c128(a, 1, o, None) for _ in range(3)]
+    assert codes[1] == -6 and codes[0] != -6 and codes[2] != -6
+    monkeypatch.setenv("PERM_FAULT", "launch")  # other stages leave this step alone
+    assert lib.perm_c128(a, 1, o, None) != -6
+    monkeypatch.delenv("PERM_FAULT")
+    assert lib.perm_c128(a, 1, o, None) != -6

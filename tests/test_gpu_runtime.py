@@ -109,3 +109,21 @@ def test_first_calls_return_before_the_work_finishes():
     assert total > 2.0
     assert second < 0.25 * total
     assert first + second < 0.5 * total
+
+
+@pytest.mark.parametrize("stage", ["launch", "finalize"])
+def test_injected_failure_then_resume(tmp_path, monkeypatch, stage):
+    """PERM_FAULT makes the third range call of a checkpointed run fail on the
+    host (no device fault); the run stops with PermError, its checkpoint holds
+    the two finished chunks, and resuming gives the uninterrupted result."""
+    A = W.haar_submatrix(22, 484, 31)
+    ref = L.run(A, str(tmp_path / "ref.json"), chunk_codes=1 << 17)
+    path = str(tmp_path / "st.json")
+    monkeypatch.setenv("PERM_FAULT", f"{stage}:3")
+    with pytest.raises(P.PermError) as e:
+        L.run(A, path, chunk_codes=1 << 17)
+    assert e.value.code == -3
+    assert L.load_state(path)["next"] == 2 << 17
+    monkeypatch.delenv("PERM_FAULT")
+    assert P.perm_last_status() == 0
+    assert L.run(A, path, chunk_codes=1 << 17) == ref
