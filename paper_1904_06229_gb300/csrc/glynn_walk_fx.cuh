@@ -9,17 +9,20 @@
 // the only rounding in a row sum is the one-time rounding of A to 2^-F_i,
 // at least as fine as a 53-bit double of the row's largest sum.
 //
-// Per code, each v_i is turned into the double w_i = v_i 2^(-F_i - 1) with
-// integer bit operations (sign, count of leading zeros, shift, exponent
-// field; truncated to 53 bits), and the product and the signed accumulation
-// run in FP64 exactly as in the floating-point walk (or, in the FP32-product
-// mode, v_i is split straight into an FP32 significand and an integer
-// exponent).
+// Per code, for complex A the first kIxRows<N> (about 0.85 n) of the v_i are
+// multiplied straight from their integers in 64-bit integer block floating
+// point (see ix_product below); each remaining v_i is turned into the double
+// w_i = v_i 2^(-F_i - 1) with integer bit operations (sign, count of leading
+// zeros, shift, exponent field; truncated to 53 bits) and multiplied in
+// FP64, and the signed accumulation runs in FP64 as in the floating-point
+// walk (in the FP32-product mode, v_i is split straight into an FP32
+// significand and an integer exponent).
 //
 // GB300 note: DFMA issues at 1/64 of the FP32 rate on this part while the
-// integer pipes run at half the FP32 rate, so moving the 2n row-update adds
-// per code to the integer pipes leaves the FP64 pipe with the 4(n-1) product
-// operations only (complex), a 1.5x reduction of its work at n = 40.
+// integer pipes run at half the FP32 rate, so the 2n row-update adds per code
+// run on the integer pipes, and so does most of the product: the FP64 pipe
+// keeps 4 (n - kIxRows) + 4 operations per complex code (28 at n = 40,
+// against 6n - 2 = 238 for FP64 row sums and products).
 #pragma once
 
 #include <cuda_runtime.h>

@@ -24,8 +24,9 @@
 // subtracts 2 C_k, a carry adds 2 gmax_k C_k back; none of this rounds.  The
 // weight is exact table values: C(gmax_0, g_0) times the product over the
 // other digits, which changes only on a carry.  The signed weight multiplies
-// the FP64 product; terms are summed like the Gray walk's (FP64 run sums
-// folded into double-double).
+// the product of the row sums, formed as in the fixed-point Gray walk (most
+// factors in integer block floating point, the rest in FP64); terms are
+// summed like the Gray walk's (FP64 run sums folded into double-double).
 #include <cuda_runtime.h>
 
 #include <cstdint>

@@ -1,4 +1,4 @@
-// Instantiations of the fixed-point-row Gray walk: complex matrices, FP64 products, orders 33..64.
+// Instantiations of the fixed-point-row Gray walk: complex matrices, products mostly in integer block floating point, orders 33..64.
 #include "glynn_walk_fx.cuh"
 
 namespace perm {

@@ -1,4 +1,4 @@
-// Instantiations of the fixed-point-row Gray walk: complex matrices, FP64 products, orders 1..32.
+// Instantiations of the fixed-point-row Gray walk: complex matrices, products mostly in integer block floating point, orders 1..32.
 #include "glynn_walk_fx.cuh"
 
 namespace perm {
