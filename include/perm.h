@@ -216,6 +216,15 @@ int perm_batch_stats(const double* const* ptrs, const int* ns, int count, double
  * perm_batch tunes lazily.  Returns PERM_OK or an error. */
 int perm_batch_autotune(int n_lo, int n_hi);
 
+/* Read (set = 0) or replace (set != 0) the batch tuning table of `device`
+ * for the row arithmetic PERM_ROWS selects: L is a HOST array of 33 ints,
+ * L[n] = codes per lane for order n (0 = not tuned yet; L[0] unused).  On
+ * set every entry must be 0 or a power of two in 16 .. 2^24 (PERM_EINVAL
+ * otherwise, nothing changed).  Host only: no CUDA call is made, so a table
+ * saved from one process can be loaded into another before its first batch
+ * (the lengths change only speed, never results beyond rounding order). */
+int perm_batch_tuning(int device, int* L, int set);
+
 /* ---- Exact permanents of small-integer matrices ----
  * Glynn's form (the App. A sum with v = 2w, an integer for integer A):
  *   2^(n-1) per(A) = (-1)^(n-1) sum_r (-1)^r prod_i v_i(x(r)),

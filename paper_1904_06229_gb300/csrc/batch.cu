@@ -468,6 +468,27 @@ int autotune_order(int dev, int n) {
 
 extern "C" {
 
+int perm_batch_tuning(int device, int* L, int set) {
+  if (!L) return PERM_ENULL;
+  if (device < 0 || device >= 64) return PERM_EINVAL;
+  if (set) {
+    // every entry 0 (not tuned) or a power of two in 16 .. 2^24 codes per lane
+    for (int n = 0; n <= kBatchNMax; ++n) {
+      const int v = L[n];
+      if (v != 0 && (v < 16 || v > (1 << 24) || (v & (v - 1)) != 0)) return PERM_EINVAL;
+    }
+  }
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  Tune& t = g_tune_tab[rows_from_env() == kRowsF64 ? 0 : 1][device];
+  for (int n = 0; n <= kBatchNMax; ++n) {
+    if (set)
+      t.L[n] = n == 0 ? 0 : L[n];
+    else
+      L[n] = t.L[n];
+  }
+  return PERM_OK;
+}
+
 int perm_batch_autotune(int n_lo, int n_hi) {
   TraceRange trace("perm_batch_autotune");
   if (n_lo < 1 || n_hi > kBatchNMax || n_lo > n_hi) return PERM_EINVAL;

@@ -46,6 +46,7 @@ EXPORTS = [
     "perm_batch",
     "perm_batch_stats",
     "perm_batch_autotune",
+    "perm_batch_tuning",
     "perm_mod01",
     "perm_crt",
     "perm_default_primes",
@@ -92,6 +93,7 @@ def load(path: Optional[str] = None):
             "perm_batch": [vp, vp, i, vp, vp],
             "perm_batch_stats": [vp, vp, i, vp, vp, vp],
             "perm_batch_autotune": [i, i],
+            "perm_batch_tuning": [i, vp, i],
             "perm_mod01": [vp, i, vp, vp, vp],
             "perm_crt": [vp, vp, i, vp],
             "perm_default_primes": [vp],
@@ -327,6 +329,54 @@ def perm_batch_stats(mats: Sequence[torch.Tensor], out: Optional[torch.Tensor] =
 
 def perm_batch_autotune(n_lo: int, n_hi: int) -> None:
     _check(load().perm_batch_autotune(int(n_lo), int(n_hi)), "perm_batch_autotune")
+
+
+def perm_batch_tuning(device: int, L: Optional[Sequence[int]] = None) -> list:
+    """Read the batch tuning table of `device` (L is None), or replace it with
+    L (33 ints, L[n] codes per lane for order n, 0 = untuned); returns the
+    table in force afterwards."""
+    buf = (ctypes.c_int * 33)()
+    if L is not None:
+        if len(L) != 33:
+            raise ValueError("33 entries expected (orders 0..32)")
+        for k, v in enumerate(L):
+            buf[k] = int(v)
+        _check(load().perm_batch_tuning(int(device), ctypes.addressof(buf), 1), "perm_batch_tuning")
+    _check(load().perm_batch_tuning(int(device), ctypes.addressof(buf), 0), "perm_batch_tuning")
+    return [int(v) for v in buf]
+
+
+def save_batch_tuning(path: str, device: int = 0, name: Optional[str] = None) -> None:
+    """Add this device's batch tuning table to the JSON file at `path`, keyed
+    by the GPU's name (torch.cuda.get_device_name unless `name` is given)."""
+    import json
+
+    key = name if name is not None else torch.cuda.get_device_name(device)
+    data = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            data = json.load(f)
+    data[key] = perm_batch_tuning(device)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def load_batch_tuning(path: str, device: int = 0, name: Optional[str] = None) -> bool:
+    """Load the table saved for this GPU's name into `device`; False when the
+    file has none for it."""
+    import json
+
+    key = name if name is not None else torch.cuda.get_device_name(device)
+    if not os.path.exists(path):
+        return False
+    with open(path) as f:
+        data = json.load(f)
+    if key not in data:
+        return False
+    perm_batch_tuning(device, data[key])
+    return True
 
 
 def perm_default_primes() -> list:
