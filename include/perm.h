@@ -144,7 +144,8 @@ int perm_f64_f32p(const double* A, int n, double* out, void* stream);
  * mult: HOST array of R multiplicities >= 1 summing to n; 1 <= R <= n <= 64;
  *    at most 2^62 terms (PERM_EINVAL otherwise).
  * out: 2 doubles (re, im), device or host.  Row sums are exact int64 fixed
- * point, products FP64, accumulation double-double; rows of A are not
+ * point, products as in perm_c128 (most factors in integer block floating
+ * point, the rest in FP64), accumulation double-double; rows of A are not
  * merged (use the transpose for repeated rows: per(A) = per(A^T)). */
 int perm_c128_repeated(const double* C, const int* mult, int R, int n, double* out, void* stream);
 
@@ -152,7 +153,8 @@ int perm_c128_repeated(const double* C, const int* mult, int R, int n, double* o
  * For A with a_ij = 0 whenever |i - j| > k: multiply the linear forms
  * C_i = sum_j a_ij x_j row by row with x_j^2 = 0, setting x_{i-k-1} = 1 once
  * no later row involves it, then all x = 1.  O(n 2^(2k+1) (2k+1)) work,
- * linear in n for fixed k.
+ * linear in n for fixed k; the kernel forms only the C(2k+1, k+1) window
+ * subsets whose size a live monomial can have.
  * A: `count` complex n x n matrices, contiguous (count * 2*n*n doubles,
  *    row-major interleaved), device or host; only entries with |i - j| <= k
  *    are read (the others are taken as zero).
@@ -189,7 +191,10 @@ int perm_sparse_partition(const double* A_host, int n, int* block, uint64_t* cou
  * items, largest order first, from an atomic ticket; per-matrix partials are
  * combined in a fixed order by a second kernel.  The launch pair is captured
  * in a CUDA graph keyed by (ns, count) and replayed on later calls with the
- * same sizes.  Chunk lengths come from a per-(GPU, n) tuning table that the
+ * same sizes.  A plan holds at most 2^26 work items (or one per matrix):
+ * larger batches get longer chunks for the orders with the most items, so
+ * any batch size runs in one launch.  Chunk lengths come from a per-(GPU, n)
+ * tuning table that the
  * library fills by timing candidates the first time an order is seen (see
  * perm_batch_autotune; PERM_BATCH_TUNE=0 in the environment takes the
  * default length without timing, as does a call made while `stream` is
