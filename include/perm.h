@@ -194,8 +194,8 @@ int perm_sparse_partition(const double* A_host, int n, int* block, uint64_t* cou
  * same sizes.  A plan holds at most 2^26 work items (or one per matrix):
  * larger batches get longer chunks for the orders with the most items, so
  * any batch size runs in one launch.  Chunk lengths come from a per-(GPU, n)
- * tuning table that the
- * library fills by timing candidates the first time an order is seen (see
+ * tuning table that the library fills by timing candidates the first time an
+ * order is seen (see
  * perm_batch_autotune; PERM_BATCH_TUNE=0 in the environment takes the
  * default length without timing, as does a call made while `stream` is
  * being captured).  Results equal perm_c128 on the same matrix to within
