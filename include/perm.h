@@ -273,8 +273,26 @@ const char* perm_status_string(int status);
 
 /* FP64 fused-multiply-add throughput of the current device, measured with
  * independent DFMA chains on every SM (blocking, about 0.1 s).  gops: lane
- * DFMA operations per second / 1e9 (one DFMA = 2 flops). */
+ * DFMA operations per second / 1e9 (one DFMA = 2 flops).  Same as
+ * perm_pipe_peak(PERM_PIPE_DFMA, gops). */
 int perm_fp64_peak(double* gops);
+
+/* Instruction kinds of perm_pipe_peak. */
+#define PERM_PIPE_DFMA 0  /* FP64 fused multiply-add, register operands */
+#define PERM_PIPE_FFMA 1  /* FP32 fused multiply-add */
+#define PERM_PIPE_FFMA2 2 /* packed FP32 fused multiply-add (two FMAs per lane instruction) */
+#define PERM_PIPE_IMAD 3  /* 32-bit integer multiply-add */
+#define PERM_PIPE_ALU 4   /* 32-bit three-input logic operation */
+#define PERM_PIPE_ISSUE 5 /* packed FP32 FMAs and logic operations interleaved: the issue rate */
+
+/* Throughput of one instruction kind on the current device: eight
+ * independent chains per thread, 8 blocks of 256 threads per SM, best of five
+ * timed launches (blocking, well under a second).  Not part of the method:
+ * it measures the roofline denominators the walk kernels are compared with.
+ * g_per_s: lane instructions per second / 1e9.  PERM_EINVAL for an unknown
+ * kind, PERM_ENULL for a null pointer, PERM_ECUDA without a device,
+ * PERM_ENOMEM if its 16 KB-per-SM sink cannot be allocated. */
+int perm_pipe_peak(int pipe, double* g_per_s);
 
 /* Free the library's per-device status words, cached graphs and the stream-
  * ordered memory pool's unused reserve.  Safe to call more than once; the

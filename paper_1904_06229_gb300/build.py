@@ -35,6 +35,10 @@ SOURCES = [
     "walk_fx_c128_f32.cu",
     "walk_fx_r64_f32.cu",
     "walk_df_c128.cu",
+    "walk_xp_c128_lo.cu",
+    "walk_xp_c128_hi.cu",
+    "walk_pdf_c128_lo.cu",
+    "walk_pdf_c128_hi.cu",
     "glynn_mod.cu",
     "mod_lo.cu",
     "mod_mid.cu",

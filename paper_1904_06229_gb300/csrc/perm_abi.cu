@@ -140,7 +140,7 @@ void ensure_kernels_loaded() {
   for (int n = 1; n <= PERM_NMAX; ++n) {
     for (int c = 0; c < 2; ++c)
       for (int m = 0; m < 2; ++m)
-        for (int r = 0; r < 3; ++r)
+        for (int r = 0; r < kRowModes; ++r)
           walk_resident_blocks(n, c != 0, m ? kProdF32 : kProdF64, (RowMode)r);  // loads the walk kernel
     if (n <= 32)
       mod_resident_lo(n);
@@ -166,12 +166,18 @@ RowMode rows_from_env() {
   const char* e = std::getenv("PERM_ROWS");
   if (e && std::strcmp(e, "fp64") == 0) return kRowsF64;
   if (e && std::strcmp(e, "df") == 0) return kRowsDf;
+  if (e && std::strcmp(e, "pair") == 0) return kRowsPair;
+  if (e && std::strcmp(e, "pdf") == 0) return kRowsPdf;
   return kRowsFixed;
 }
 
 int walk_resident_blocks(int n, bool cplx, ProductMode mode, RowMode rows) {
   if (rows == kRowsDf && cplx && mode == kProdF64) return walk_blocks_df_c128(n);
-  if (rows == kRowsDf) rows = kRowsFixed;
+  if (rows == kRowsPair && cplx && mode == kProdF64)
+    return n <= 32 ? walk_blocks_xp_c128_lo(n) : walk_blocks_xp_c128_hi(n);
+  if (rows == kRowsPdf && cplx && mode == kProdF64)
+    return n <= 32 ? walk_blocks_pdf_c128_lo(n) : walk_blocks_pdf_c128_hi(n);
+  if (rows == kRowsDf || rows == kRowsPair || rows == kRowsPdf) rows = kRowsFixed;
   if (rows == kRowsFixed) {
     if (mode == kProdF64) {
       if (cplx) return n <= 32 ? walk_blocks_fx_c128_f64_lo(n) : walk_blocks_fx_c128_f64_hi(n);
@@ -188,7 +194,11 @@ int walk_resident_blocks(int n, bool cplx, ProductMode mode, RowMode rows) {
 
 cudaError_t walk_launch(bool cplx, ProductMode mode, const WalkArgs& a, RowMode rows) {
   if (rows == kRowsDf && cplx && mode == kProdF64) return walk_launch_df_c128(a);
-  if (rows == kRowsDf) rows = kRowsFixed;
+  if (rows == kRowsPair && cplx && mode == kProdF64)
+    return a.n <= 32 ? walk_launch_xp_c128_lo(a) : walk_launch_xp_c128_hi(a);
+  if (rows == kRowsPdf && cplx && mode == kProdF64)
+    return a.n <= 32 ? walk_launch_pdf_c128_lo(a) : walk_launch_pdf_c128_hi(a);
+  if (rows == kRowsDf || rows == kRowsPair || rows == kRowsPdf) rows = kRowsFixed;
   if (rows == kRowsFixed) {
     if (mode == kProdF64) {
       if (cplx) return a.n <= 32 ? walk_launch_fx_c128_f64_lo(a) : walk_launch_fx_c128_f64_hi(a);

@@ -25,10 +25,16 @@ enum RowMode : int {
   kRowsFixed = 1,  // exact int64 fixed-point row sums, integer updates (glynn_walk_fx.cuh)
   kRowsDf = 2,     // double-float row sums and products on the FP32 pipe (glynn_walk_df.cuh);
                    // complex FP64-product walks only, the others use kRowsFixed
+  kRowsPair = 3,   // exact float-pair row sums, packed double-float products (glynn_walk_xp.cuh);
+                   // complex FP64-product walks only, the others use kRowsFixed
+  kRowsPdf = 4,    // packed double-float row sums re-seeded from exact int64 and packed double-float
+                   // products (glynn_walk_xp.cuh); complex FP64-product walks only
 };
+constexpr int kRowModes = 5;
 
 // Row arithmetic for the floating-point entry points: PERM_ROWS=fp64 selects
-// kRowsF64, PERM_ROWS=df kRowsDf, anything else (default) kRowsFixed.
+// kRowsF64, PERM_ROWS=df kRowsDf, PERM_ROWS=pair kRowsPair, PERM_ROWS=pdf kRowsPdf,
+// anything else (default) kRowsFixed.
 RowMode rows_from_env();
 
 struct WalkArgs {
@@ -57,6 +63,14 @@ cudaError_t walk_launch_c128_f32(const WalkArgs& a);      // n in 1..64
 cudaError_t walk_launch_r64_f32(const WalkArgs& a);       // n in 1..64
 cudaError_t walk_launch_df_c128(const WalkArgs& a);  // double-float rows and products
 int walk_blocks_df_c128(int n);
+cudaError_t walk_launch_xp_c128_lo(const WalkArgs& a);  // exact float-pair rows, packed products, n in 1..32
+cudaError_t walk_launch_xp_c128_hi(const WalkArgs& a);  // n in 33..64
+int walk_blocks_xp_c128_lo(int n);
+int walk_blocks_xp_c128_hi(int n);
+cudaError_t walk_launch_pdf_c128_lo(const WalkArgs& a);  // packed double-float rows and products, n in 1..32
+cudaError_t walk_launch_pdf_c128_hi(const WalkArgs& a);  // n in 33..64
+int walk_blocks_pdf_c128_lo(int n);
+int walk_blocks_pdf_c128_hi(int n);
 cudaError_t walk_launch_fx_c128_f64_lo(const WalkArgs& a);  // fixed-point rows
 cudaError_t walk_launch_fx_c128_f64_hi(const WalkArgs& a);
 cudaError_t walk_launch_fx_r64_f64(const WalkArgs& a);
@@ -123,7 +137,7 @@ int device_status_word(int dev, int** out);
 void batch_release_plans();
 
 // ---- peak probe ----
-cudaError_t dfma_probe_launch(double* sink, int blocks, int iters, cudaStream_t stream);
+cudaError_t pipe_probe_launch(int pipe, double* sink, int blocks, int iters, cudaStream_t stream);
 
 // ---- tracing and host-side fault injection ----
 // NVTX range named after a C ABI entry point, open for the duration of the

@@ -53,6 +53,7 @@ EXPORTS = [
     "perm_last_status",
     "perm_status_string",
     "perm_fp64_peak",
+    "perm_pipe_peak",
     "perm_shutdown",
 ]
 
@@ -100,6 +101,7 @@ def load(path: Optional[str] = None):
             "perm_last_status": [vp],
             "perm_status_string": [i],
             "perm_fp64_peak": [vp],
+            "perm_pipe_peak": [i, vp],
             "perm_shutdown": [],
         }.items():
             fn = getattr(lib, name)
@@ -424,6 +426,17 @@ def perm_fp64_peak() -> float:
     """Measured FP64 DFMA rate of the current device, in Gop/s (lane DFMAs)."""
     v = ctypes.c_double(0.0)
     _check(load().perm_fp64_peak(ctypes.addressof(v)), "perm_fp64_peak")
+    return float(v.value)
+
+
+PIPES = {"dfma": 0, "ffma": 1, "ffma2": 2, "imad": 3, "alu": 4, "issue": 5}
+
+
+def perm_pipe_peak(pipe: str) -> float:
+    """Measured throughput of one instruction kind (see PIPES) on the current
+    device, in G lane instructions/s."""
+    v = ctypes.c_double(0.0)
+    _check(load().perm_pipe_peak(PIPES[pipe], ctypes.addressof(v)), "perm_pipe_peak")
     return float(v.value)
 
 
