@@ -38,6 +38,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "perm_oracle.c")
+_SRC_PAPER = os.path.join(_HERE, "paper_scheme.c")  # the paper's double + Kahan CPU scheme (benchmark baseline)
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _XL = 8  # 64-bit limbs of the exact integer form
 _lib = None
@@ -46,11 +47,12 @@ _lock = threading.Lock()
 
 def build(force: bool = False) -> str:
     """Compile perm_oracle.c into oracle/_build/liboracle.so (gcc, OpenMP)."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_PAPER))
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
-               "-o", tmp, _SRC]
+               "-o", tmp, _SRC, _SRC_PAPER]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -75,6 +77,7 @@ def _load():
                                               ld_p]
             lib.oracle_ryser2_c.argtypes = [ld_p, ctypes.c_int, ctypes.c_int, ld_p, ld_p, ld_p]
             lib.oracle_sparse_c.argtypes = [ld_p, ctypes.c_int, ld_p, ld_p, ld_p]
+            lib.paper_scheme_range.argtypes = [ld_p, ctypes.c_int, u64, u64, ctypes.c_int, ctypes.c_int, ld_p]
             _lib = lib
     return _lib
 
@@ -177,6 +180,20 @@ def glynn_partial_parts(A, first: int, count: int, parts: int, threads: int = 0)
     with ThreadPoolExecutor(max_workers=workers) as ex:
         res = list(ex.map(lambda fr: glynn_partial(A, fr[0], fr[1]), ranges))
     return _compensated([r[0] for r in res]), _compensated([r[1] for r in res]), _compensated([r[2] for r in res])
+
+
+def paper_scheme_partial(A, first: int, count: int, parts: int, threads: int = 0):
+    """The paper's CPU scheme (Sec. 2.B: double row sums and products, Kahan
+    summation, consecutive parts in parallel, partials added in order) over
+    the code range [first, first + count): sum (-1)^r prod_i w_i as a
+    complex.  A benchmark baseline, not a parity reference."""
+    a = _as_c128(A)
+    out = np.zeros(2, dtype=np.float64)
+    rc = _load().paper_scheme_range(_ptr(a), a.shape[0], int(first), int(count), int(parts), int(threads),
+                                    _ptr(out))
+    if rc != 0:
+        raise ValueError("bad range")
+    return complex(out[0], out[1])
 
 
 def _compensated(xs):

@@ -15,8 +15,9 @@
 // uses more than 2048 blocks, so any order 1..PERM_NMAX fits; larger orders
 // are rejected with PERM_EINVAL.  Host code cannot use the array's name as a
 // device address, so the first call on each device (with that device
-// current) looks the address up with cudaGetSymbolAddress and caches it.
-// That first call should therefore come before any stream capture.
+// current) looks the address up with cudaGetSymbolAddress and caches it; it
+// also loads the library's kernels on that device.  That first call should
+// therefore come before any stream capture or latency-critical use.
 //
 // Every call on a device shares the one array and leaves its contents behind:
 // the status word is cleared by each call and the partial slots are
@@ -87,6 +88,9 @@ extern "C" int perm_c128_noalloc(const double* A, int n, double* out, void* stre
   // inputs and outputs must already be on the device: staging a host buffer
   // would need an allocation
   if (!device_readable(A) || !device_readable(out)) return PERM_EINVAL;
+  // load every kernel of the library on this device first (once), so that no
+  // launch below waits for a lazy module load behind running work
+  ensure_kernels_loaded();
   double* scratch = nullptr;
   int rc = scratch_address(dev, &scratch);
   if (rc) return rc;

@@ -167,8 +167,8 @@ RowMode rows_from_env() {
   if (e && std::strcmp(e, "fp64") == 0) return kRowsF64;
   if (e && std::strcmp(e, "df") == 0) return kRowsDf;
   if (e && std::strcmp(e, "pair") == 0) return kRowsPair;
-  if (e && std::strcmp(e, "pdf") == 0) return kRowsPdf;
-  return kRowsFixed;
+  if (e && std::strcmp(e, "fixed") == 0) return kRowsFixed;
+  return kRowsPdf;  // complex FP64-product walks; the others take kRowsFixed
 }
 
 int walk_resident_blocks(int n, bool cplx, ProductMode mode, RowMode rows) {

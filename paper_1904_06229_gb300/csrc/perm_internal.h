@@ -33,8 +33,9 @@ enum RowMode : int {
 constexpr int kRowModes = 5;
 
 // Row arithmetic for the floating-point entry points: PERM_ROWS=fp64 selects
-// kRowsF64, PERM_ROWS=df kRowsDf, PERM_ROWS=pair kRowsPair, PERM_ROWS=pdf kRowsPdf,
-// anything else (default) kRowsFixed.
+// kRowsF64, PERM_ROWS=df kRowsDf, PERM_ROWS=pair kRowsPair, PERM_ROWS=fixed
+// kRowsFixed, anything else (default) kRowsPdf, which the walks without a
+// packed variant (real, FP32-product, batch) take as kRowsFixed.
 RowMode rows_from_env();
 
 struct WalkArgs {

@@ -20,9 +20,13 @@ def _batch(mats):
     return out.cpu().numpy(), dm
 
 
-def test_batch_vs_single_and_oracle():
+def test_batch_vs_single_and_oracle(monkeypatch):
+    """The batch walks exact fixed-point rows; each result equals a single
+    perm_c128 launch with the same row arithmetic (PERM_ROWS=fixed) to
+    rounding, and the oracle to 1e-10."""
     ns, mats = W.batch_study(300, seed=11, n_lo=1, n_hi=20)
     out, dm = _batch(mats)
+    monkeypatch.setenv("PERM_ROWS", "fixed")
     for k in range(len(mats)):
         single = P.perm_c128(dm[k]).cpu().numpy()
         got = complex(out[k, 0], out[k, 1])

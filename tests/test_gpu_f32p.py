@@ -42,15 +42,17 @@ def test_f64_f32p_within_bound(n):
     assert abs(got - float(r[0])) <= _bound(n, float(r[2]))
 
 
-def test_config_real_gaussian_n32():
-    """Precision study: real N(0,1) n = 32 (seed 4), FP32 products vs FP64."""
+def test_config_real_gaussian_n32_vs_fp64():
+    """Precision study: real N(0,1) n = 32 (seed 4), FP32 products against the
+    FP64 path (both are checked against the stored oracle value in
+    test_gpu_golden.py); the relative difference is reported."""
     A = W.real_gaussian(32, 4)
     t = torch.from_numpy(A).cuda()
     f64 = float(P.perm_f64(t).cpu().numpy()[0])
     f32p = float(P.perm_f64_f32p(t).cpu().numpy()[0])
     rel = abs(f32p - f64) / abs(f64)
     print(f"n=32 real Gaussian: FP64 {f64!r} FP32-product {f32p!r} rel diff {rel:.3e}")
-    assert rel < 1e-2
+    assert rel < 1e-4
 
 
 def test_config_pm1_n30_exact_reference():

@@ -1,19 +1,26 @@
-"""Edge cases of the complex product's integer block floating point (most
-factors of each term multiplied from the exact int64 row sums): exponent
-bookkeeping across rows of very different scale, row sums that are exactly
-zero at many codes, and integer matrices whose permanent is known exactly."""
+"""Edge cases of the complex walks' row scaling and product arithmetic (the
+default packed double-float walk and the exact fixed-point walk with its
+integer block floating point): exponent bookkeeping across rows of very
+different scale, row sums that are exactly zero at many codes, and integer
+matrices whose permanent is known exactly."""
 import numpy as np
 import pytest
 import torch
 
+import _tolerance as T
 from oracle import oracle as O
 from paper_1904_06229_gb300 import perm as P
 from paper_1904_06229_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-REL = 1e-10
-U64 = 2.0 ** -53
+REL = T.REL
+
+
+@pytest.fixture(autouse=True, params=["pdf", "fixed"])
+def rows(request, monkeypatch):
+    monkeypatch.setenv("PERM_ROWS", request.param)
+    return request.param
 
 
 def gpu_c128(A):
@@ -44,18 +51,18 @@ def test_integer_matrices_exact(n):
         ex = O.per_exact(A)
         got = gpu_c128(A.astype(np.float64))
         assert got.imag == 0.0
+        print(f"integer matrix n={n}: rel err {abs(got.real - ex) / abs(ex) if ex else abs(got.real):.3e}")
         assert abs(got.real - ex) <= REL * abs(ex) if ex else got.real == 0.0
 
 
 @pytest.mark.parametrize("n", [12, 18])
-def test_complex_unit_entries(n):
+def test_complex_unit_entries(n, rows):
     """Entries in {1, -1, i, -i} against the long-double oracle and the
     transpose."""
     k = np.random.default_rng(70 + n).integers(0, 4, size=(n, n))
     A = (1j) ** k
     re, im, asum = O.per(A)
     ref = complex(float(re), float(im))
-    got = gpu_c128(A)
-    tol = max(REL * abs(ref), 64 * n * U64 * float(asum))
-    assert abs(got - ref) <= tol
-    assert abs(gpu_c128(A.T) - ref) <= tol
+    u = T.unit(rows)
+    T.check(gpu_c128(A), ref, float(asum), n, u, f"unit entries n={n}")
+    T.check(gpu_c128(A.T), ref, float(asum), n, u, f"unit entries n={n}, transpose")

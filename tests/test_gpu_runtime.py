@@ -84,7 +84,7 @@ def test_first_calls_return_before_the_work_finishes():
     CUDA loads kernels lazily and a load waits for the device to go idle, so
     the library loads all of its kernels when it first meets a device; a
     second call made while the first one's walk is still running (here a
-    modular walk behind an n = 35 FP64 walk of about 4 s) must not wait for
+    modular walk behind an n = 37 FP64 walk of about 5 s) must not wait for
     it."""
     import subprocess
     import sys
@@ -93,7 +93,7 @@ def test_first_calls_return_before_the_work_finishes():
     script = (
         "import time, torch\n"
         "from paper_1904_06229_gb300 import perm as P, workloads as W\n"
-        "A = torch.from_numpy(W.complex_gaussian(35, 7)).cuda()\n"
+        "A = torch.from_numpy(W.complex_gaussian(37, 7)).cuda()\n"
         "B = torch.from_numpy(W.zero_one(24, 6)).cuda()\n"
         "pr = P.perm_default_primes()\n"
         "torch.cuda.synchronize()\n"

@@ -1,19 +1,21 @@
 """perm_c128_noalloc, the variant for callers that cannot allocate device
 memory (it keeps its partial sums in a static array inside the library),
-called through the C ABI and compared with perm_c128 on two calls in a row.
-This file is collected last on purpose."""
+called through the C ABI on two calls in a row and compared with perm_c128
+and with the CPU oracle.  This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
 import pytest
 import torch
 
+import _tolerance as T
+from oracle import oracle as O
 from paper_1904_06229_gb300 import perm as P
 from paper_1904_06229_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-REL = 1e-10  # the FP64 parity tolerance of the other tests
+REL = T.REL  # the FP64 parity tolerance of the other tests
 
 
 def _call(lib, A, n, out):
@@ -28,6 +30,8 @@ def test_noalloc_matches_perm_c128_twice(n, seed):
     A = torch.from_numpy(W.complex_gaussian(n, seed)).cuda()
     ref = P.perm_c128(A).cpu().numpy()
     refc = complex(ref[0], ref[1])
+    re, im, asum = O.per(W.complex_gaussian(n, seed))
+    oracle = complex(float(re), float(im))
     for _ in range(2):
         out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
         assert _call(lib, A, n, out) == 0
@@ -35,6 +39,7 @@ def test_noalloc_matches_perm_c128_twice(n, seed):
         o = out.cpu().numpy()
         got = complex(o[0], o[1])
         assert abs(got - refc) <= REL * abs(refc), (n, got, refc)
+        T.check(got, oracle, float(asum), n, T.U_DF, f"perm_c128_noalloc n={n}")
 
 
 def test_noalloc_rejects_bad_arguments():
