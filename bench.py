@@ -1,22 +1,37 @@
 """Benchmark: Gray-code Glynn permanent throughput on the n = 40 complex128
 Haar workload (S(1600, 40): sqrt(1600) times the top-left 40 x 40 block of a
-Haar unitary of order 1600), as terms/s and against the measured FP64 DFMA
-rate; the batched random-matrix study (perms/s, batched vs one launch per
-matrix) on a sample; the CPU oracle as baseline.
+Haar unitary of order 1600), as terms/s, against the roofline of the pipe
+that bounds the walk kernel, with the CPU oracle and the paper's own CPU
+scheme as baselines.
 
 A step is one pass of the whole hot path (stage A, seed, Gray walk with
 product / signed accumulate / row update, double-double reduction) over one
 slice of 2^33 consecutive Gray codes of the n = 40 sum: 64 such slices make
 up the whole permanent (2^39 codes), and step s covers slice (rank, s) of
-it.  Under torchrun each rank walks its own slices (weak scaling; the
-partials' exchange is a 32-byte host gather after timing).
+it.  Under torchrun each rank walks its own slices (weak scaling); after
+timing, rank 0 gathers every rank's 32-byte partials, adds them in rank
+order (multirank.combine_partials) and checks the sum against its own
+walk of the same slices.
 
-Besides the contract's keys the JSON line carries: alt_rows (the FP64-row
-and double-float walks on the same slice), batch (a sample of the batch
-study, batched vs one launch per matrix), exact (0-1 permanents n = 30, 36),
-precision (FP32 products vs FP64), next_rows (repeated-column, sparse and
-band timings), stats (batch statistics), err_vs_oracle, and with
---batch-study COUNT the whole batch study in one launch (batch_study).
+Besides the contract's keys the JSON line carries:
+  roofline       FP32-pipe roofline of the default walk kernel (packed FMAs),
+                 the issue-slot fraction, and the FP64-equivalent rate of the
+                 survey's 6n - 4 operations per term
+  alt_rows       the other row arithmetics on the same slice
+  n48            n = 48 Haar S(2304, 48): one 2^34-code slice, and the error
+                 against the oracle on a 2^18-code slice
+  c1_n20         the 20 x 20 complex Gaussian (seed 0): time per permanent and
+                 error against the oracle
+  exact          0-1 permanents n = 30, 36 modulo four 62-bit primes, checked
+                 bit for bit against the stored oracle values
+  precision      FP32 products vs FP64 (real Gaussian n = 32, +-1 n = 30)
+                 against the stored oracle values
+  next_rows      repeated-column, sparse and band timings
+  stats          batch statistics of the circular-entry family
+  batch          batched vs one launch per matrix on a 2000-matrix sample
+  batch_study    the whole 200,000-matrix study in one launch (--batch-study 0
+                 skips it)
+  err_vs_oracle, cpu_baseline, cpu_baseline_paper
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                     [--batch-sample M] [--batch-study COUNT]
@@ -42,12 +57,20 @@ N_ORDER = 40
 SEED = 1040
 CODES_PER_STEP = 1 << 33
 L2_FLUSH_BYTES = 256 << 20
+GOLDEN = os.path.join(ROOT, "tests", "golden", "configs.json")
+
+# Lane instructions per code of the default walk at n = 40, from ncu's
+# smsp__inst_executed.sum x 32 / codes on one 2^30-code launch of the same
+# kernel (profiles/k_walk_xp_pdf_c128_n40_haar.md); the issue-slot fraction
+# below divides it by the scheduler rate of 4 warp instructions per clock
+# per SM at the SM clock sampled during the run.
+ISSUED_LANE_INSTR_PER_CODE_N40 = 1368
 
 
-def workload_matrix():
+def workload_matrix(n=N_ORDER, seed=SEED):
     from paper_1904_06229_gb300 import workloads as W
 
-    return W.haar_submatrix(N_ORDER, N_ORDER * N_ORDER, SEED)
+    return W.haar_submatrix(n, n * n, seed)
 
 
 def config_dict(world):
@@ -60,6 +83,11 @@ def config_dict(world):
         "l2": "flushed between steps (256 MiB write); the 25.6 KB input is staged to shared memory once per block",
         "parallelism": f"gray-range shards x{world}",
     }
+
+
+def load_golden():
+    with open(GOLDEN) as f:
+        return json.load(f)["cases"]
 
 
 # ------------------------------------------------------------------ helpers
@@ -177,11 +205,96 @@ def run_reference(args):
     return 0
 
 
+def cpu_paper_sample(A, first, count_hint, oracle_ref, target_s: float = 8.0):
+    """The paper's own CPU scheme (Sec. 2.B: double row sums and products,
+    Kahan summation, consecutive parts in parallel) on all host cores, on a
+    slice of the same sum starting at `first`; its error against the oracle on
+    the oracle's slice [first, first + count_hint)."""
+    from oracle import oracle as O
+
+    cores = os.cpu_count() or 1
+    got = O.paper_scheme_partial(A, first, count_hint, parts=cores, threads=cores)
+    ref = complex(float(oracle_ref[0]), float(oracle_ref[1]))
+    err = abs(got - ref) / abs(ref)
+    count = 1 << 20
+    t0 = time.perf_counter()
+    O.paper_scheme_partial(A, first, count, parts=cores, threads=cores)
+    dt = time.perf_counter() - t0
+    count = int(min(1 << 34, max(count, count * target_s / max(dt, 1e-3))))
+    count = max(cores, count - count % cores)
+    t0 = time.perf_counter()
+    O.paper_scheme_partial(A, first, count, parts=cores, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": count / dt, "unit": "terms/s", "cores": cores, "kind": "paper scheme",
+            "sample": f"codes [2^30, 2^30+{count}) of the n={A.shape[0]} sum: double row sums and products, Kahan "
+                      f"summation, {cores} parts on {cores} threads (Sec. 2.B)",
+            "seconds": dt, "rel_err_vs_oracle": err, "err_slice": [first, count_hint]}
+
+
 # ------------------------------------------------------------------ GPU arm
+def pdf_fp32_ops(n):
+    """FP32 lane operations per code of the default walk (packed double-float
+    rows and products, glynn_walk_xp.cuh), counted from its arithmetic: per
+    row pair and Gray step an 11-operation double-float add on each of the two
+    components (two rows per packed operation); per term NP - 1 packed complex
+    double-float products of 32 packed operations, 4-operation packed
+    renormalisations (every 8 factors of a chain, and at its end), and one
+    scalar complex double-float product of 32 operations joining the lanes."""
+    NP = (n + 1) // 2
+    CP = 2 if NP >= 2 else 1
+    lens, ren = [1] * CP, CP
+    for k in range(CP, NP):
+        q = k % CP
+        lens[q] += 1
+        if lens[q] % 8 == 0 and k + CP < NP:
+            ren += 1
+    muls = (NP - CP) + (1 if CP == 2 else 0)
+    return NP * 2 * 11 * 2 + muls * 32 * 2 + ren * 4 * 2 + 32
+
+
+def roofline_of(rows, n, codes, launch_s, peaks, sms, clk_mhz):
+    """Roofline of the walk kernel for the row arithmetic in use."""
+    ops64 = 6 * n - 4  # the survey's algorithmic FP64-pipe operations per term
+    fp64_equiv = {"ops_per_term": ops64, "gops": codes * ops64 / launch_s / 1e9,
+                  "vs_dfma_peak": codes * ops64 / launch_s / 1e9 / peaks["dfma"],
+                  "note": "FP64-equivalent rate of the survey's 6n-4 FP64 operations per term; not a roofline "
+                          "fraction: the default walk does this work in double-float on the FP32 pipe"}
+    if rows in ("pdf",):
+        ops = pdf_fp32_ops(n)
+        achieved = codes * ops / launch_s / 1e9
+        peak = 2.0 * peaks["ffma2"]  # packed FMA: two FP32 operations per lane instruction
+        out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP32 lane-op/s",
+               "frac": achieved / peak, "traffic": None,
+               "kernel": f"perm::k_walk_xp<{n}, false> (packed double-float rows and products, f32x2 FMA pipe)",
+               "rows": rows, "fp32_ops_per_term": ops,
+               "peak_source": "measured this run: perm_pipe_peak(FFMA2) x 2 FP32 operations (MEASURED_PEAKS.json has "
+                              "no FP32 figure)",
+               "traffic_note": "the walk reads its 25.6 KB matrix once per block; ncu measured 0.15 MB read + 11.8 MB "
+                               "written per 2^30-code launch (profiles/), independent of the codes per launch"}
+        if n == N_ORDER and clk_mhz:
+            ipc = ISSUED_LANE_INSTR_PER_CODE_N40
+            out["issue_frac"] = codes * ipc / launch_s / (128.0 * sms * clk_mhz * 1e6)
+            out["issued_lane_instr_per_term"] = ipc
+    else:
+        issued = {"fp64": 6 * n - 2, "df": 8, "pair": 8}.get(rows)
+        if rows == "fixed":
+            k_ix = min((n * 17) // 20, n - 2) if n >= 8 else 0
+            issued = 4 * (n - k_ix) + 4 if k_ix else 4 * (n - 1) + 2
+        out = {"bound": "alu", "achieved": codes * issued / launch_s / 1e9, "peak": peaks["dfma"],
+               "unit": "G FP64 lane-op/s", "frac": codes * issued / launch_s / 1e9 / peaks["dfma"],
+               "traffic": None, "rows": rows, "fp64_issued_per_term": issued,
+               "peak_source": "measured this run: perm_pipe_peak(DFMA)",
+               "note": "FP64 instructions issued per term over the DFMA rate; the binding resource of this row "
+                       "arithmetic is described in DESIGN.md"}
+    out["fp64_equivalent"] = fp64_equiv
+    return out
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
 
+    from paper_1904_06229_gb300 import multirank as M
     from paper_1904_06229_gb300 import perm as P
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -200,6 +313,7 @@ def run_gpu(args):
     P.load()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     A = workload_matrix()
     dA = torch.from_numpy(A.astype(np.complex128)).to(dev)
     out = torch.empty(4, dtype=torch.float64, device=dev)
@@ -207,13 +321,13 @@ def run_gpu(args):
     total_codes = 1 << (N_ORDER - 1)
     nslices = total_codes // CODES_PER_STEP
 
-    def slice_first(step):
-        return ((rank + world * step) % nslices) * CODES_PER_STEP
+    def slice_first(step, r=None):
+        return (((rank if r is None else r) + world * step) % nslices) * CODES_PER_STEP
 
-    peak_gops = P.perm_fp64_peak()
-    rows = os.environ.get("PERM_ROWS", "fixed")
-    if rows not in ("fp64", "df"):
-        rows = "fixed"
+    peaks = {k: P.perm_pipe_peak(k) for k in ("dfma", "ffma", "ffma2", "issue")}
+    rows = os.environ.get("PERM_ROWS", "pdf")
+    if rows not in ("fixed", "fp64", "df", "pair"):
+        rows = "pdf"
 
     # warm-up
     for w in range(args.warmup):
@@ -272,91 +386,42 @@ def run_gpu(args):
         e2e_el = float(tt.item())
     e2e_value = CODES_PER_STEP * e2e_steps * world / e2e_el
 
-    # fixed-order host gather of the partials (the exchange step of a split sum)
+    # the exchange step of a split sum: rank 0 gathers every rank's partials,
+    # adds them in rank order and checks the result against its own walk of
+    # the same slices
+    multirank = None
     if world > 1:
         gathered = [None] * world
         dist.all_gather_object(gathered, [p.cpu().tolist() for p in partials])
+        if rank == 0:
+            combined = M.combine_partials(gathered, N_ORDER)
+            own = []
+            for r in range(world):
+                mine = []
+                for s in range(args.steps):
+                    o = P.perm_c128_range(dA, slice_first(args.warmup + s, r), CODES_PER_STEP).cpu().tolist()
+                    mine.append(o)
+                own.append(mine)
+            single = M.combine_partials(own, N_ORDER)
+            multirank = {"ranks": world, "slices": world * args.steps, "combined": [combined.real, combined.imag],
+                         "rel_diff_vs_rank0_walk": abs(combined - single) / abs(single)}
 
     n = N_ORDER
-    ops_per_term = 6 * n - 4     # algorithmic FP64 pipe ops: 4(n-1) product + 2n row update
-    flops_per_term = 8 * n - 6   # complex multiply = 6 flops, complex add = 2
-    # FP64 instructions the kernel actually issues per code: with fixed-point
-    # rows the 2n row updates run on the integer pipes, and the first
-    # min(17n/20, n - 2) factors (kIxRows in glynn_walk_fx.cuh) are multiplied
-    # in integer block floating point, which joins the FP64 chains as one
-    # complex factor
-    k_ix = min((n * 17) // 20, n - 2) if n >= 8 else 0
-    fixed_issued = 4 * (n - k_ix) + 4 if k_ix else 4 * (n - 1) + 2
-    issued = {"fixed": fixed_issued, "fp64": 6 * n - 2, "df": 8}[rows]
     avg_launch = sum(launch_s) / len(launch_s)
-    achieved = CODES_PER_STEP * ops_per_term / avg_launch / 1e9
-    kname = {"fixed": f"perm::k_walk_fx<{n}, complex, FP64 product> (int64 fixed-point rows; {k_ix} of the "
-                      f"factors in 64-bit integer block floating point)",
-             "fp64": f"perm::k_walk<{n}, complex, FP64 product> (FP64 rows)",
-             "df": f"perm::k_walk_df<{n}> (double-float rows and products, FP32 pipe)"}[rows]
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
-                "frac": achieved / peak_gops, "traffic": None,
-                "kernel": kname, "rows": rows,
-                "ops_per_term": ops_per_term,
-                "fp64_issued_per_term": issued,
-                "fp64_pipe_frac": CODES_PER_STEP * issued / avg_launch / 1e9 / peak_gops,
-                "flop_frac": CODES_PER_STEP * flops_per_term / avg_launch / (2e9 * peak_gops),
-                "peak_source": "measured this run: perm_fp64_peak() DFMA probe (MEASURED_PEAKS.json has no FP64 "
-                               "figure)",
-                "note": "achieved counts the algorithmic 6n-4 FP64-pipe ops per code; with fixed-point rows the "
-                        "2n row-update adds run exactly on the integer pipes and half of the product's factors are "
-                        "multiplied in 64-bit integer block floating point, so frac exceeds 1 while the FP64 pipe "
-                        "itself runs at fp64_pipe_frac"}
+    clk_mhz = clk["sm_mhz"] if clk else None
+    roofline = roofline_of(rows, n, CODES_PER_STEP, avg_launch, peaks, sms, clk_mhz)
     line = {"metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(world), "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": "terms/s", "h2d_bytes_per_step": 16 * n * n,
                     "d2h_bytes_per_step": 32, "steps": e2e_steps},
-            "gpu_launches": 2 * args.steps, "clocks": clk, "fp64_peak_gops": peak_gops}
-
-    if rank == 0 and not args.no_alt_rows:
-        # one step of each other arithmetic on the same slice, for comparison
-        line["alt_rows"] = []
-        ref_part = out.clone()
-        P.perm_c128_range(dA, slice_first(args.warmup), CODES_PER_STEP, out=ref_part)
-        for alt in [m for m in ("fixed", "fp64", "df") if m != rows]:
-            os.environ["PERM_ROWS"] = alt
-            P.perm_c128_range(dA, slice_first(0), CODES_PER_STEP, out=out)
-            torch.cuda.synchronize()
-            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a0.record(stream)
-            P.perm_c128_range(dA, slice_first(args.warmup), CODES_PER_STEP, out=out)
-            a1.record(stream)
-            torch.cuda.synchronize()
-            at = a0.elapsed_time(a1) / 1e3
-            alt_issued = {"fixed": fixed_issued, "fp64": 6 * n - 2, "df": 8}[alt]
-            o, rp = out.cpu().numpy(), ref_part.cpu().numpy()
-            va, vr_ = complex(o[0] + o[1], o[2] + o[3]), complex(rp[0] + rp[1], rp[2] + rp[3])
-            line["alt_rows"].append({"rows": alt, "terms_per_s": CODES_PER_STEP / at,
-                                     "frac": CODES_PER_STEP * ops_per_term / at / 1e9 / peak_gops,
-                                     "fp64_pipe_frac": CODES_PER_STEP * alt_issued / at / 1e9 / peak_gops,
-                                     "rel_diff_vs_default": abs(va - vr_) / abs(vr_)})
-        os.environ["PERM_ROWS"] = rows
-    if rank == 0 and args.batch_sample > 0:
-        line["batch"] = batch_measure(P, torch, dev, args.batch_sample)
-    if rank == 0 and args.batch_study > 0:
-        line["batch_study"] = batch_study_measure(P, torch, dev, args.batch_study)
-    if rank == 0 and not args.no_extras:
-        line["exact"] = exact_measure(P, torch, dev)
-        line["precision"] = precision_measure(P, torch, dev)
-        line["next_rows"] = next_rows_measure(P, torch, dev)
-        line["stats"] = stats_measure(P, torch, dev)
-    if rank == 0 and not args.no_cpu_baseline:
-        cb, (first, count, g) = cpu_oracle_sample(A)
-        line["cpu_baseline"] = cb
-        # error of the GPU on the very slice the oracle walked
-        o = P.perm_c128_range(dA, first, count).cpu().numpy()
-        got = complex(o[0] + o[1], o[2] + o[3])
-        ref = complex(float(g[0]), float(g[1]))
-        line["err_vs_oracle"] = {"slice": [first, count], "rel": abs(got - ref) / abs(ref),
-                                 "kappa_slice": float(g[2]) / abs(ref)}
+            "gpu_launches": 2 * args.steps, "clocks": clk,
+            "pipe_peaks_g_per_s": peaks, "pdf_tile_log": int(os.environ.get("PERM_PDF_TILE_LOG", "0")) or None}
+    if multirank is not None:
+        line["multirank"] = multirank
     if rank == 0:
+        extras(args, line, P, torch, dev, dA, A, rows, peaks, stream, slice_first)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -367,6 +432,7 @@ def _timed(torch, fn, reps=2):
     fn()
     torch.cuda.synchronize()
     best = float("inf")
+    r = None
     for _ in range(reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -377,13 +443,95 @@ def _timed(torch, fn, reps=2):
     return best, r
 
 
-def exact_measure(P, torch, dev):
-    """Exact 0-1 permanents (density 1/2; n = 30 seed 6, n = 36 seed 7) modulo
-    four 62-bit primes, CRT on the host."""
+def extras(args, line, P, torch, dev, dA, A, rows, peaks, stream, slice_first):
+    """Every other measurement of the JSON line (rank 0, after the timed region)."""
+    if not args.no_alt_rows:
+        line["alt_rows"] = alt_rows_measure(P, torch, dA, rows, slice_first(args.warmup))
+    if not args.no_extras:
+        line["n48"] = n48_measure(P, torch, dev)
+        line["c1_n20"] = c1_measure(P, torch, dev)
+        line["exact"] = exact_measure(P, torch, dev)
+        line["precision"] = precision_measure(P, torch, dev)
+        line["next_rows"] = next_rows_measure(P, torch, dev)
+        line["stats"] = stats_measure(P, torch, dev)
+    if args.batch_sample > 0:
+        line["batch"] = batch_measure(P, torch, dev, args.batch_sample)
+    if args.batch_study > 0:
+        line["batch_study"] = batch_study_measure(P, torch, dev, args.batch_study)
+    if not args.no_cpu_baseline:
+        cpu_leg(line, P, torch, dev, dA, A)
+
+
+def alt_rows_measure(P, torch, dA, rows, first):
+    """The other row arithmetics on the bench's own slice: rate and relative
+    difference from the default's partial sum."""
+    out = []
+    ref = P.perm_c128_range(dA, first, CODES_PER_STEP).cpu().numpy()
+    vr = complex(ref[0] + ref[1], ref[2] + ref[3])
+    for alt in [m for m in ("fixed", "fp64", "df", "pair") if m != rows]:
+        os.environ["PERM_ROWS"] = alt
+        try:
+            P.perm_c128_range(dA, 0, 1 << 24)
+            torch.cuda.synchronize()
+            at, o = _timed(torch, lambda: P.perm_c128_range(dA, first, CODES_PER_STEP), reps=1)
+            o = o.cpu().numpy()
+            va = complex(o[0] + o[1], o[2] + o[3])
+            out.append({"rows": alt, "terms_per_s": CODES_PER_STEP / at, "rel_diff_vs_default": abs(va - vr) / abs(vr)})
+        finally:
+            os.environ["PERM_ROWS"] = rows
+    return out
+
+
+def n48_measure(P, torch, dev):
+    """n = 48 Haar S(2304, 48), seed 1048: one 2^34-code slice of its 2^47-code
+    sum in one call (the whole sum would be 8192 such slices)."""
+    A48 = torch.from_numpy(workload_matrix(48, 1048)).to(dev)
+    first, count = 5 << 34, 1 << 34
+    P.perm_c128_range(A48, 0, 1 << 24)
+    torch.cuda.synchronize()
+    t, o = _timed(torch, lambda: P.perm_c128_range(A48, first, count), reps=1)
+    o = o.cpu().numpy()
+    return {"workload": "n=48 complex128 Haar S(2304,48) seed 1048, codes [5*2^34, 6*2^34)", "codes": count,
+            "seconds": t, "terms_per_s": count / t, "whole_permanent_hours": (1 << 47) / (count / t) / 3600.0,
+            "partial": [o[0] + o[1], o[2] + o[3]]}
+
+
+def c1_measure(P, torch, dev):
+    """The 20 x 20 complex Gaussian of seed 0 (2^19 codes): device time per
+    permanent (CUDA events over 20 back-to-back calls) and host latency of one
+    call including the copy back."""
     from paper_1904_06229_gb300 import workloads as W
 
-    import os
+    A20 = torch.from_numpy(W.complex_gaussian(20, 0)).to(dev)
+    out = torch.empty(2, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        P.perm_c128(A20, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        P.perm_c128(A20, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    dev_us = e0.elapsed_time(e1) * 1e3 / 20
+    lat = []
+    for _ in range(10):
+        h0 = time.perf_counter()
+        v = P.perm_c128(A20, out=out).cpu().numpy()
+        lat.append(time.perf_counter() - h0)
+    return {"workload": "n=20 complex Gaussian N(0,1/2)+iN(0,1/2) seed 0", "us_per_permanent": dev_us,
+            "host_latency_us": statistics.median(lat) * 1e6, "terms_per_s": (1 << 19) / (dev_us * 1e-6),
+            "value": [float(v[0]), float(v[1])]}
 
+
+def exact_measure(P, torch, dev):
+    """Exact 0-1 permanents (density 1/2; n = 30 seed 6, n = 36 seed 7) modulo
+    four 62-bit primes, CRT on the host; each checked bit for bit against the
+    stored oracle value (tests/golden/configs.json), also through the
+    modular group walk."""
+    from paper_1904_06229_gb300 import workloads as W
+
+    golden = load_golden()
     primes = P.perm_default_primes()
     out = {}
     for n, seed in ((30, 6), (36, 7)):
@@ -391,7 +539,6 @@ def exact_measure(P, torch, dev):
         res = torch.empty(4, dtype=torch.int64, device=dev)
         sec, _ = _timed(torch, lambda: P.perm_mod01(t, primes, res))
         val = P.perm_crt([int(v) for v in res.cpu()], primes)
-        # the same residues through the modular group walk (no exact sums)
         old = os.environ.get("PERM_MOD_SUM")
         os.environ["PERM_MOD_SUM"] = "modular"
         try:
@@ -402,33 +549,73 @@ def exact_measure(P, torch, dev):
                 del os.environ["PERM_MOD_SUM"]
             else:
                 os.environ["PERM_MOD_SUM"] = old
-        out[f"n{n}"] = {"seconds": sec, "codes_per_s": (1 << (n - 1)) / sec, "per_bits": val.bit_length(),
-                        "per_mod_1e9+7": val % 1000000007,
+        ref = int(golden[f"zero_one_n{n}_seed{seed}"]["per"])
+        out[f"n{n}"] = {"seconds": sec, "codes_per_s": (1 << (n - 1)) / sec, "per": str(val),
+                        "per_bits": val.bit_length(), "matches_oracle": val == ref,
                         "modular_walk": {"seconds": sec_m, "codes_per_s": (1 << (n - 1)) / sec_m,
                                          "same_residues": res_m.cpu().tolist() == res.cpu().tolist()}}
     return out
 
 
 def precision_measure(P, torch, dev):
-    """FP32-product variant vs FP64: real N(0,1) n = 32 (seed 4) and +-1 n = 30
-    (seed 5, against the exact integer from the modular path)."""
+    """FP32-product variant vs FP64 against the stored oracle values: real
+    N(0,1) n = 32 (seed 4, long-double oracle) and +-1 n = 30 (seed 5, exact
+    integer); the FP32 variant's stated bound is (2n + 2) 2^-24 sum|t|."""
     from paper_1904_06229_gb300 import workloads as W
 
+    golden = load_golden()
     out = {}
+    g = golden["real_gaussian_n32_seed4"]
+    ref, asum = float(g["per"]), float(g["abs_sum"])
     A = torch.from_numpy(W.real_gaussian(32, 4)).to(dev)
     t64, r64 = _timed(torch, lambda: P.perm_f64(A).cpu())
     t32, r32 = _timed(torch, lambda: P.perm_f64_f32p(A).cpu())
-    f64, f32 = float(r64[0]), float(r32[0])
-    out["real_gaussian_n32"] = {"fp64_s": t64, "f32p_s": t32, "f32p_rel_diff_vs_fp64": abs(f32 - f64) / abs(f64)}
-    B = W.bernoulli_pm1(30, 5)
-    primes = P.perm_default_primes()
-    exact = P.perm_crt([int(v) for v in P.perm_mod01(torch.from_numpy(B).to(dev), primes).cpu()], primes)
-    Bd = torch.from_numpy(B.astype(np.float64)).to(dev)
-    t64, r64 = _timed(torch, lambda: P.perm_f64(Bd).cpu())
-    t32, r32 = _timed(torch, lambda: P.perm_f64_f32p(Bd).cpu())
+    out["real_gaussian_n32"] = {"fp64_s": t64, "f32p_s": t32, "kappa": asum / abs(ref),
+                                "fp64_rel_err": abs(float(r64[0]) - ref) / abs(ref),
+                                "f32p_rel_err": abs(float(r32[0]) - ref) / abs(ref),
+                                "f32p_stated_bound": 66 * 2.0 ** -24 * asum / abs(ref)}
+    g = golden["pm1_n30_seed5"]
+    exact = int(g["per"])
+    B = torch.from_numpy(W.bernoulli_pm1(30, 5).astype(np.float64)).to(dev)
+    t64, r64 = _timed(torch, lambda: P.perm_f64(B).cpu())
+    t32, r32 = _timed(torch, lambda: P.perm_f64_f32p(B).cpu())
     out["pm1_n30"] = {"exact": str(exact), "fp64_rel_err": abs(float(r64[0]) - exact) / abs(exact),
                       "f32p_rel_err": abs(float(r32[0]) - exact) / abs(exact), "fp64_s": t64, "f32p_s": t32}
+    if "abs_sum" in g:
+        out["pm1_n30"]["f32p_stated_bound"] = 62 * 2.0 ** -24 * float(g["abs_sum"]) / abs(exact)
     return out
+
+
+def cpu_leg(line, P, torch, dev, dA, A):
+    """The CPU baselines (the oracle as it stands, the paper's own scheme) and
+    the GPU's error against the oracle on the same slices and configurations."""
+    from oracle import oracle as O
+    from paper_1904_06229_gb300 import workloads as W
+
+    cb, (first, count, g) = cpu_oracle_sample(A)
+    line["cpu_baseline"] = cb
+    o = P.perm_c128_range(dA, first, count).cpu().numpy()
+    got = complex(o[0] + o[1], o[2] + o[3])
+    ref = complex(float(g[0]), float(g[1]))
+    line["err_vs_oracle"] = {"slice": [first, count], "rel": abs(got - ref) / abs(ref),
+                             "kappa_slice": float(g[2]) / abs(ref)}
+    line["cpu_baseline_paper"] = cpu_paper_sample(A, first, count, g)
+    cores = os.cpu_count() or 1
+    if "n48" in line:
+        A48 = workload_matrix(48, 1048)
+        f48, c48 = (1 << 46) + 12345, 1 << 18
+        g48 = O.glynn_partial_parts(A48, f48, c48, parts=cores, threads=cores)
+        o = P.perm_c128_range(torch.from_numpy(A48).to(dev), f48, c48).cpu().numpy()
+        r48 = complex(float(g48[0]), float(g48[1]))
+        line["n48"]["err_vs_oracle"] = {"slice": [f48, c48],
+                                        "rel": abs(complex(o[0] + o[1], o[2] + o[3]) - r48) / abs(r48),
+                                        "kappa_slice": float(g48[2]) / abs(r48)}
+    if "c1_n20" in line:
+        r = O.per(W.complex_gaussian(20, 0))
+        ref = complex(float(r[0]), float(r[1]))
+        v = line["c1_n20"]["value"]
+        line["c1_n20"]["rel_err_vs_oracle"] = abs(complex(v[0], v[1]) - ref) / abs(ref)
+        line["c1_n20"]["kappa"] = float(r[2]) / abs(ref)
 
 
 def next_rows_measure(P, torch, dev):
@@ -582,11 +769,11 @@ def main():
     ap.add_argument("--reference-step-seconds", type=float, default=10.0,
                     help="host seconds per step of the reference arm (the CPU oracle)")
     ap.add_argument("--batch-sample", type=int, default=2000)
-    ap.add_argument("--batch-study", type=int, default=0,
-                    help="also run the whole batch study (e.g. 200000 matrices) in one launch; minutes")
+    ap.add_argument("--batch-study", type=int, default=200000,
+                    help="matrices of the whole batch study, run in one launch after the timed region (0 skips)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-alt-rows", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the exact-path and precision measurements")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other configurations' measurements")
     ap.add_argument("--codes-log2", type=int, default=33,
                     help="codes per step (2^k); smaller values make a short case for profiling")
     args = ap.parse_args()

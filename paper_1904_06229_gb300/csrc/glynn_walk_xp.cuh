@@ -59,7 +59,7 @@ namespace perm {
 
 constexpr int kXpGrid = 47;       // exact float-pair rows: multiples of 2^-47 of the row scale
 constexpr int kPdfGrid = 61;      // double-float rows: exact int64 seeds in units of 2^-61 of the row scale
-constexpr int kPdfTileLog = 7;    // double-float rows: re-seeded every 2^7 codes
+// double-float rows: re-seeded every 2^tile_log codes (a kernel argument: pdf_tile_log())
 constexpr int kXpAlignLog = 8;    // thread ranges are congruent modulo 2^8 codes
 constexpr int kXpRenormEvery = 8; // chain renormalisation period (factors)
 
@@ -333,7 +333,9 @@ __device__ __forceinline__ bool xp_stage_exact(const double* __restrict__ A, flo
 }
 
 // Stage for double-float rows: Q_ij = rint(a_ij 2^(G_i + 61)) (|Q| <= 2^61),
-// the int64 columns 2 Q_ij (sQ, [j][k][lane] = (re, im)) and seeds
+// the int64 columns 2 Q_ij (sQ, [k][j][lane] = (re, im): pair-major, so the
+// lanes of a warp re-seeding the same pair at different codes read entries
+// 32 bytes apart instead of a whole column stride) and seeds
 // v0_i = Q_in - sum_{j<n} Q_ij (sV0, [k][lane]), and the +c / -c tables with
 // c_ij the double-float rounding of 2 Q_ij 2^-61.  Returns whether any entry
 // is non-finite.
@@ -364,7 +366,7 @@ __device__ __forceinline__ bool xp_stage_df(const double* __restrict__ A, float4
       fM[base + lane] = -h;
       fM[base + 2 + lane] = -l;
     }
-    sQ[((size_t)j * NP + k) * 2 + lane] = make_longlong2(q2[0], q2[1]);
+    sQ[((size_t)k * N + j) * 2 + lane] = make_longlong2(q2[0], q2[1]);
   }
   if (N & 1) {
     // the missing row of an odd order: constant 1 (seed 2^61, columns zero)
@@ -375,7 +377,7 @@ __device__ __forceinline__ bool xp_stage_df(const double* __restrict__ A, float4
         fP[base + 1] = 0.f, fP[base + 3] = 0.f;
         fM[base + 1] = 0.f, fM[base + 3] = 0.f;
       }
-      sQ[((size_t)j * NP + (NP - 1)) * 2 + 1] = make_longlong2(0, 0);
+      sQ[((size_t)(NP - 1) * N + j) * 2 + 1] = make_longlong2(0, 0);
     }
     if (threadIdx.x == 0) sV0[(NP - 1) * 2 + 1] = make_longlong2(1ll << kPdfGrid, 0);
   }
@@ -423,7 +425,7 @@ __device__ __forceinline__ void pdf_seed(P4 (&v)[kPairs<N>], const longlong2* __
     while (x) {
       const int j = __ffsll((long long)x) - 1;
       x &= x - 1;
-      const longlong2* q = sQ + ((size_t)j * NP + k) * 2;
+      const longlong2* q = sQ + ((size_t)k * N + j) * 2;
       const longlong2 qa = q[0], qb = q[1];
       a.x += qa.x;
       a.y += qa.y;
@@ -441,13 +443,16 @@ __device__ __forceinline__ void pdf_seed(P4 (&v)[kPairs<N>], const longlong2* __
   for (int k = 0; k < NP; ++k) v[k] = seed[k];
 }
 
-// Per-thread code range: equal lengths rounded up to a multiple of 2^kXpAlignLog,
-// so every thread starts at a code congruent to `first` modulo 2^kXpAlignLog.
+// Per-thread code range: equal lengths rounded up to a multiple of an
+// alignment a (2^kXpAlignLog, or the power of two at or above the length when
+// that is smaller, so that short launches still use every thread), so every
+// thread starts at a code congruent to `first` modulo a.
 __device__ __forceinline__ void thread_range_congruent(uint64_t first, uint64_t count, uint64_t& r, uint64_t& end) {
   const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  constexpr uint64_t kA = 1ull << kXpAlignLog;
   uint64_t L = (count + T - 1) / T;
+  uint64_t kA = 1ull << kXpAlignLog;
+  while (kA > 1 && (kA >> 1) >= L) kA >>= 1;
   L = (L + kA - 1) & ~(kA - 1);
   const uint64_t s = g * L;
   r = first + (s < count ? s : count);
@@ -512,18 +517,18 @@ __device__ __forceinline__ void thread_walk_xp_exact(const float4* __restrict__ 
   }
 }
 
-// Double-float rows: every 2^kPdfTileLog codes (counted from the thread's
+// Double-float rows: every 2^tile_log codes (counted from the thread's
 // start, so the lanes of a warp re-seed together) the rows are re-seeded from
 // their exact int64 values; in between, double-float updates.
 template <int N>
 __device__ __forceinline__ void thread_walk_xp_df(const float4* __restrict__ sP, const float4* __restrict__ sM,
                                                   const longlong2* __restrict__ sQ,
                                                   const longlong2* __restrict__ sV0, uint64_t r, const uint64_t end,
-                                                  dd& accr, dd& acci) {
+                                                  int tile_log, dd& accr, dd& acci) {
   constexpr int NP = kPairs<N>;
   P4 v[NP];
   while (r < end) {
-    const uint64_t tile_end = min(end, r + (uint64_t)(1u << kPdfTileLog));
+    const uint64_t tile_end = min(end, r + (uint64_t)(1ull << tile_log));
     pdf_seed<N>(v, sQ, sV0, r);
     double sr = 0.0, si = 0.0;
     uint32_t odd = (uint32_t)(r & 1ull);
@@ -545,7 +550,7 @@ __device__ __forceinline__ void thread_walk_xp_df(const float4* __restrict__ sP,
 template <int N, bool EXACT>
 __global__ void __launch_bounds__(kWalkThreads) k_walk_xp(const double* __restrict__ A, uint64_t first,
                                                           uint64_t count, double* __restrict__ partials,
-                                                          int accumulate, int* __restrict__ status) {
+                                                          int accumulate, int* __restrict__ status, int tile_log) {
   using Shape = XpShape<N, EXACT>;
   constexpr int NP = kPairs<N>;
   extern __shared__ __align__(16) float4 xsm[];
@@ -570,7 +575,8 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk_xp(const double* __restri
       thread_walk_xp_exact<N>(sP, sM, reinterpret_cast<const float4*>(seed), r, end, accr, acci);
     else
       thread_walk_xp_df<N>(sP, sM, reinterpret_cast<const longlong2*>(seed),
-                           reinterpret_cast<const longlong2*>(seed) + (size_t)N * NP * 2, r, end, accr, acci);
+                           reinterpret_cast<const longlong2*>(seed) + (size_t)N * NP * 2, r, end, tile_log, accr,
+                           acci);
     // prod_i w_i = prod_i u_i 2^(-N - sum_i G_i)   (u_i = 2 w_i 2^G_i)
     int gs = 0;
     for (int i = 0; i < N; ++i) gs += sG[i];
@@ -624,7 +630,7 @@ struct XpKernel {
     cudaError_t e = prepare(resident);
     if (e != cudaSuccess) return e;
     k_walk_xp<N, EXACT><<<a.blocks, kWalkThreads, smem, a.stream>>>(a.A, a.first, a.count, a.partials,
-                                                                     a.accumulate, a.status);
+                                                                     a.accumulate, a.status, pdf_tile_log());
     return cudaGetLastError();
   }
 };

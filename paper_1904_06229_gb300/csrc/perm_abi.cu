@@ -171,6 +171,15 @@ RowMode rows_from_env() {
   return kRowsPdf;  // complex FP64-product walks; the others take kRowsFixed
 }
 
+int pdf_tile_log() {
+  const char* e = std::getenv("PERM_PDF_TILE_LOG");
+  if (e && *e) {
+    const int v = std::atoi(e);
+    if (v >= 4 && v <= 16) return v;
+  }
+  return kPdfTileLog;
+}
+
 int walk_resident_blocks(int n, bool cplx, ProductMode mode, RowMode rows) {
   if (rows == kRowsDf && cplx && mode == kProdF64) return walk_blocks_df_c128(n);
   if (rows == kRowsPair && cplx && mode == kProdF64)

@@ -38,6 +38,11 @@ constexpr int kRowModes = 5;
 // packed variant (real, FP32-product, batch) take as kRowsFixed.
 RowMode rows_from_env();
 
+// Re-seed period (log2 codes) of the packed double-float walk: PERM_PDF_TILE_LOG
+// (4..16) or the default kPdfTileLog.
+constexpr int kPdfTileLog = 10;
+int pdf_tile_log();
+
 struct WalkArgs {
   const double* A;     // device, row-major (interleaved re/im when complex)
   int n;               // order
