@@ -200,20 +200,34 @@ int perm_sparse_partition(const double* A_host, int n, int* block, uint64_t* cou
  * ptrs: DEVICE array of `count` DEVICE pointers, each to a 2*n_k*n_k complex
  *       matrix; ns: HOST array of the `count` orders (1 <= n_k <= 32);
  * out:  DEVICE array of 2*count doubles (re, im per matrix).
- * All permanents run in one persistent kernel that takes (matrix, chunk) work
- * items, largest order first, from an atomic ticket; per-matrix partials are
- * combined in a fixed order by a second kernel.  The launch pair is captured
- * in a CUDA graph keyed by (ns, count) and replayed on later calls with the
- * same sizes.  A plan holds at most 2^26 work items (or one per matrix):
- * larger batches get longer chunks for the orders with the most items, so
- * any batch size runs in one launch.  Chunk lengths come from a per-(GPU, n)
- * tuning table that the library fills by timing candidates the first time an
- * order is seen (see
- * perm_batch_autotune; PERM_BATCH_TUNE=0 in the environment takes the
- * default length without timing, as does a call made while `stream` is
- * being captured).  Results equal perm_c128 on the same matrix to within
+ * The matrices are grouped by order, largest first, and each order's
+ * (matrix, code chunk) work items go to one of three persistent kernels: one
+ * warp per item with exact fixed-point rows, or one block of 128 threads per
+ * item with the default packed double-float walk (a variant allowing two or
+ * three blocks per SM); each kernel takes its items from an atomic ticket,
+ * and a last kernel adds each matrix's item partials in a fixed order.  The
+ * kernel and the codes per thread of each order come from a per-GPU tuning
+ * table (perm_batch_autotune, perm_batch_tuning); untuned orders take
+ * built-in choices.  With PERM_ROWS=fixed or fp64 every order takes the
+ * warp kernel with that row arithmetic.
+ * The launches are captured in a CUDA graph (a plan) keyed by device,
+ * stream, row arithmetic, the orders ns and the tuning; ptrs and out are
+ * passed through a small device argument block set just before each graph
+ * launch, so later calls with the same orders reuse the plan for any
+ * matrices and output.  Building a plan allocates its buffers stream-ordered
+ * on `stream` and uploads the order-sorted matrix positions through kernel
+ * arguments: the call never waits for the device.  Up to 8 plans are kept;
+ * dropping one (or perm_shutdown) frees its buffers with cudaFree, which
+ * waits for launches still using them.  A plan holds at most 2^26 work items
+ * (or one per matrix): larger batches get longer chunks for the orders with
+ * the most items, so any batch size runs in one graph launch.  Results equal
+ * perm_c128 on the same matrix with the same row arithmetic to within
  * rounding of the summation order. */
 int perm_batch(const double* const* ptrs, const int* ns, int count, double* out, void* stream);
+
+/* Number of batch plans built so far in this process (host only): a call
+ * that reuses a cached plan leaves it unchanged. */
+int perm_batch_plans(int* built);
 
 /* ---- Batch with the random-matrix statistics of Secs. 3-6 ----
  * perm_batch, then, per order n = 0..32, statistics of X = |per(A)| / sqrt(n!)
@@ -230,18 +244,26 @@ int perm_batch(const double* const* ptrs, const int* ns, int count, double* out,
 int perm_batch_stats(const double* const* ptrs, const int* ns, int count, double* out, double* stats, void* stream);
 
 /* Fill the batch tuning table for orders n_lo..n_hi on the current device by
- * timing candidate chunk lengths on synthetic input (blocking).  Optional:
- * perm_batch tunes lazily.  Returns PERM_OK or an error. */
+ * timing, per order, each kernel (warp per item, block per item with up to
+ * 255 or 168 registers) at each chunk length 16 .. 8192 codes per thread on
+ * synthetic input (blocking, a few seconds).  Returns PERM_OK or an error. */
 int perm_batch_autotune(int n_lo, int n_hi);
 
+/* Batch kernel kinds of the tuning table. */
+#define PERM_BATCH_WARP 1  /* one warp per item, exact fixed-point rows */
+#define PERM_BATCH_CTA 2   /* one block of 128 threads per item, packed double-float walk, 2 blocks per SM */
+#define PERM_BATCH_CTA3 3  /* the same with 3 blocks per SM (168 registers) */
+
 /* Read (set = 0) or replace (set != 0) the batch tuning table of `device`
- * for the row arithmetic PERM_ROWS selects: L is a HOST array of 33 ints,
- * L[n] = codes per lane for order n (0 = not tuned yet; L[0] unused).  On
- * set every entry must be 0 or a power of two in 16 .. 2^24 (PERM_EINVAL
- * otherwise, nothing changed).  Host only: no CUDA call is made, so a table
- * saved from one process can be loaded into another before its first batch
- * (the lengths change only speed, never results beyond rounding order). */
-int perm_batch_tuning(int device, int* L, int set);
+ * for the row arithmetic PERM_ROWS selects: L and kind are HOST arrays of 33
+ * ints; for order n, kind[n] is the kernel (PERM_BATCH_*) and L[n] the codes
+ * per thread (per lane for the warp kernel), both 0 when not tuned (index 0
+ * unused).  On set every entry must be 0 in both arrays or a power of two in
+ * 16 .. 2^24 with a kind 1..3 (PERM_EINVAL otherwise, nothing changed).
+ * Host only: no CUDA call is made, so a table saved from one process can be
+ * loaded into another before its first batch (the choices change only speed,
+ * never results beyond rounding order). */
+int perm_batch_tuning(int device, int* L, int* kind, int set);
 
 /* ---- Exact permanents of small-integer matrices ----
  * Glynn's form (the App. A sum with v = 2w, an integer for integer A):

@@ -47,6 +47,8 @@ SOURCES = [
     "band.cu",
     "sparse.cu",
     "batch.cu",
+    "batch_cta2.cu",
+    "batch_cta3.cu",
     "perm_abi.cu",
     "peak.cu",
     "noalloc.cu",

@@ -1,20 +1,32 @@
 // Batched permanents: many independent complex matrices of uneven order in
-// one persistent launch (the random-matrix studies of Secs. 3-6 compute
+// one graph launch (the random-matrix studies of Secs. 3-6 compute
 // 10^5..10^7 permanents of orders up to ~35 each).
 //
-// Work is cut into (matrix, code range) items of 32 lanes x L codes, L tuned
-// per order; the host sorts items by decreasing order (largest work first)
-// and each warp of the persistent grid pulls the next item from an atomic
-// ticket, stages that matrix into its own shared-memory slot, walks its range
-// with the same per-thread Gray walk as the single-matrix kernel, and writes
-// a double-double partial per item.  A second kernel adds each matrix's item
-// partials in item order (deterministic) and applies 2 (-1)^(n-1).  The pair
-// of launches (plus the ticket reset) is captured once per (device, stream,
-// pointers, orders) into a CUDA graph and replayed.
+// Layout.  The host groups the matrices by order, largest first (a counting
+// sort: `perm` lists matrix indices by position), and describes each order in
+// a BatchTable: which kernel walks it, the codes per work item, the items per
+// matrix, and where its items' tickets and partials start.  Items are never
+// listed: a kernel decodes a ticket into (order, matrix, code chunk) from the
+// table (batch_common.cuh), so a plan is O(count) to build and holds one int
+// per matrix plus four doubles per item.
 //
-// Tuning: for each order n the codes-per-lane L is chosen by timing the
-// candidates on a synthetic batch the first time n is seen (or by
-// perm_batch_autotune); PERM_BATCH_TUNE=0 keeps the built-in default.
+// Kernels.  Orders go to one of three persistent kernels, chosen per order by
+// the tuner: one warp per item with exact fixed-point rows (k_batch here; its
+// lanes share an item, so small orders need little staging), or one block of
+// 128 threads per item with the packed double-float walk (batch_cta.cuh,
+// allowing 2 or 3 blocks per SM).  Each kernel pulls tickets from its own
+// counter, largest orders first.  A finalize kernel adds each matrix's item
+// partials in item order (deterministic) and applies 2 (-1)^(n-1).
+//
+// Asynchrony.  The pointers of a call (matrix pointer array, output) are
+// written into a 16-byte device argument block by a one-thread kernel just
+// before the graph launch, so one cached plan (keyed by device, stream,
+// orders and tuning) serves any matrices of that shape.  A new plan's buffers
+// come from stream-ordered allocations on the caller's stream and its
+// position list is uploaded by kernels whose parameters carry the data (no
+// pinned staging, no synchronous copy), so perm_batch never waits for the
+// device.  Tuning (perm_batch_autotune) is the one blocking step; untuned
+// orders take built-in defaults.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -29,6 +41,7 @@
 #include <mutex>
 #include <vector>
 
+#include "batch_common.cuh"
 #include "glynn_walk.cuh"
 #include "glynn_walk_fx.cuh"
 #include "perm.h"
@@ -36,7 +49,6 @@
 
 namespace perm {
 
-constexpr int kBatchNMax = 32;
 constexpr int kBatchThreads = 128;
 constexpr int kBatchWarps = kBatchThreads / 32;
 // Per-warp shared slot (16-byte units): the FP64-row walk keeps A (n^2) and
@@ -62,21 +74,23 @@ __device__ __forceinline__ void batch_walk_case(int n, double2* slot, uint64_t r
   }
 }
 
+// One warp per item: the warp stages its item's matrix into its own slot and
+// its 32 lanes walk consecutive shares of the item's codes.
 template <int ROWS>
-__global__ void __launch_bounds__(kBatchThreads) k_batch(const double* const* __restrict__ ptrs,
-                                                         const BatchItem* __restrict__ items, int nitems,
-                                                         double* __restrict__ item_partials,
-                                                         unsigned int* __restrict__ ticket, int* __restrict__ status) {
+__global__ void __launch_bounds__(kBatchThreads)
+    k_batch(const BatchArgs* __restrict__ ba, const int* __restrict__ perm, const __grid_constant__ BatchTable tab,
+            double* __restrict__ partials, unsigned long long* __restrict__ ticket, int* __restrict__ status) {
   extern __shared__ __align__(16) double2 bsm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double2* slot = bsm + (size_t)warp * kBatchSlot;
+  const double* const* ptrs = ba->ptrs;
   for (;;) {
-    unsigned int it = 0;
-    if (lane == 0) it = atomicAdd(ticket, 1u);
-    it = __shfl_sync(0xffffffffu, it, 0);
-    if (it >= (unsigned int)nitems) break;
-    const BatchItem item = items[it];
-    const int n = (int)item.n;
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(ticket, 1ull);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    BatchItemRef item;
+    if (!batch_decode(tab, kBatchWarp, perm, t, item)) break;
+    const int n = item.n;
     const double2* __restrict__ A = reinterpret_cast<const double2*>(ptrs[item.matrix]);
     bool bad = false;
     if constexpr (ROWS == kRowsFixed) {
@@ -121,7 +135,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const double* const* __
     accr = dd_warp_sum(accr);
     acci = dd_warp_sum(acci);
     if (lane == 0) {
-      double* o = item_partials + (size_t)it * 4;
+      double* o = partials + item.partial * 4;
       o[0] = accr.hi;
       o[1] = accr.lo;
       o[2] = acci.hi;
@@ -131,54 +145,60 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const double* const* __
   }
 }
 
-// out[2k..2k+1] = 2 (-1)^(n_k - 1) * sum of matrix k's item partials, in item order.
-__global__ void k_batch_finalize(const double* __restrict__ item_partials, const int* __restrict__ mat_first,
-                                 const int* __restrict__ mat_items, const int* __restrict__ mat_n, int count,
-                                 double* __restrict__ out) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= count) return;
+// Order of the matrix at position i (orders are grouped, largest first).
+__device__ __forceinline__ int order_at(const BatchTable& tab, int i) {
+  for (int m = kBatchNMax; m >= 1; --m)
+    if (tab.kind[m] != kBatchNone && i >= tab.mstart[m] && i < tab.mstart[m] + tab.mcount[m]) return m;
+  return 0;
+}
+
+// out[2k..2k+1] = 2 (-1)^(n_k - 1) * sum of matrix k's item partials, in item
+// order; one thread per position.
+__global__ void k_batch_finalize(const BatchArgs* __restrict__ ba, const int* __restrict__ perm,
+                                 const __grid_constant__ BatchTable tab, const double* __restrict__ partials,
+                                 int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int n = order_at(tab, i);
+  if (n == 0) return;
+  const uint64_t ipm = tab.items_per_matrix[n];
+  const uint64_t f = tab.gbase[n] + (uint64_t)(i - tab.mstart[n]) * ipm;
   dd ar{0.0, 0.0}, ai{0.0, 0.0};
-  const int f = mat_first[k], c = mat_items[k];
-  for (int t = 0; t < c; ++t) {
-    const double* p = item_partials + (size_t)(f + t) * 4;
+  for (uint64_t t = 0; t < ipm; ++t) {
+    const double* p = partials + (f + t) * 4;
     ar = dd_add(ar, dd{p[0], p[1]});
     ai = dd_add(ai, dd{p[2], p[3]});
   }
-  const double s = ((mat_n[k] - 1) & 1) ? -2.0 : 2.0;
+  const int k = perm[i];
+  const double s = ((n - 1) & 1) ? -2.0 : 2.0;
+  double* out = ba->out;
   out[2 * k] = s * __dadd_rn(ar.hi, ar.lo);
   out[2 * k + 1] = s * __dadd_rn(ai.hi, ai.lo);
 }
 
-template <int ROWS>
-int batch_resident_blocks_t() {
-  static std::atomic<int> cached[64];  // per device; filled once, read from any host thread
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-  if (cached[dev]) return cached[dev];
-  if (cudaFuncSetAttribute(k_batch<ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) !=
-      cudaSuccess)
-    return 0;
-  int per_sm = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<ROWS>, kBatchThreads, kBatchSmem) !=
-      cudaSuccess)
-    return 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  cached[dev] = (per_sm < 1 ? 1 : per_sm) * sms;
-  return cached[dev];
+// Device copy of a host int array, carried in the kernel's parameters (so the
+// upload is stream-ordered without pinned host memory).
+constexpr int kUploadInts = 4000;
+struct UploadChunk {
+  int v[kUploadInts];
+};
+
+__global__ void k_upload(int* __restrict__ dst, const __grid_constant__ UploadChunk c, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = c.v[i];
 }
 
-int batch_resident_blocks_rows(RowMode rows) {
-  return rows == kRowsF64 ? batch_resident_blocks_t<kRowsF64>() : batch_resident_blocks_t<kRowsFixed>();
+__global__ void k_set_args(BatchArgs* __restrict__ ba, const double* const* ptrs, double* out) {
+  ba->ptrs = ptrs;
+  ba->out = out;
 }
-
-int batch_resident_blocks() { return batch_resident_blocks_rows(rows_from_env()); }
 
 // ---- statistics of X = |per| / sqrt(n!) per order (Secs. 3-6) ----
 // stats[n * PERM_STATS_STRIDE + ...]: [0] count, [1..4] sum X^1..X^4,
 // [5 + b] histogram: b = 0 for X < 1e-4, b = 1..96 for
 // 10^(-4 + (b-1)/16) <= X < 10^(-4 + b/16) (16 bins per decade), b = 97 for
-// X >= 100.  One block per order; every sum is formed in a fixed order
-// (double-double per thread, fixed tree), counts are integer atomics.
+// X >= 100.  One block per order, over that order's positions; every sum is
+// formed in a fixed order (double-double per thread, fixed tree), counts are
+// integer atomics.
 constexpr int kStatsEdges = 97;  // 10^(-4 + j/16), j = 0..96
 constexpr int kStatsStride = 5 + kStatsEdges + 1;
 
@@ -187,8 +207,9 @@ struct StatsParams {
   double edges[kStatsEdges];
 };
 
-__global__ void __launch_bounds__(256) k_batch_stats(const double* __restrict__ out, const int* __restrict__ ns,
-                                                     int count, StatsParams sp, double* __restrict__ stats) {
+__global__ void __launch_bounds__(256)
+    k_batch_stats(const BatchArgs* __restrict__ ba, const int* __restrict__ perm, const __grid_constant__ BatchTable tab,
+                  StatsParams sp, double* __restrict__ stats) {
   const int n = blockIdx.x;
   __shared__ unsigned int hist[kStatsEdges + 1];
   __shared__ unsigned int cnt;
@@ -198,8 +219,11 @@ __global__ void __launch_bounds__(256) k_batch_stats(const double* __restrict__ 
   __syncthreads();
   dd m1{0, 0}, m2{0, 0}, m3{0, 0}, m4{0, 0};
   unsigned int c = 0;
-  for (int k = threadIdx.x; k < count; k += blockDim.x) {
-    if (ns[k] != n) continue;
+  const double* out = ba->out;
+  const int lo_pos = n >= 1 && tab.kind[n] != kBatchNone ? tab.mstart[n] : 0;
+  const int hi_pos = n >= 1 && tab.kind[n] != kBatchNone ? tab.mstart[n] + tab.mcount[n] : 0;
+  for (int i = lo_pos + (int)threadIdx.x; i < hi_pos; i += blockDim.x) {
+    const int k = perm[i];
     const double re = out[2 * (size_t)k], im = out[2 * (size_t)k + 1];
     const double x = sqrt(re * re + im * im) * sp.inv_sqrt_fact[n];
     const double x2 = x * x;
@@ -244,9 +268,58 @@ __global__ void __launch_bounds__(256) k_batch_stats(const double* __restrict__ 
   for (int b = threadIdx.x; b <= kStatsEdges; b += blockDim.x) st[5 + b] = (double)hist[b];
 }
 
+template <int ROWS>
+int batch_resident_blocks_t() {
+  static std::atomic<int> cached[64];  // per device; filled once, read from any host thread
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (cached[dev]) return cached[dev];
+  if (cudaFuncSetAttribute(k_batch<ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) !=
+      cudaSuccess)
+    return 0;
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<ROWS>, kBatchThreads, kBatchSmem) !=
+      cudaSuccess)
+    return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  cached[dev] = (per_sm < 1 ? 1 : per_sm) * sms;
+  return cached[dev];
+}
+
+int batch_resident_blocks_rows(RowMode rows) {
+  return rows == kRowsF64 ? batch_resident_blocks_t<kRowsF64>() : batch_resident_blocks_t<kRowsFixed>();
+}
+
+int batch_resident_blocks_cta(int kind) {
+  return kind == kBatchCta3 ? batch_resident_cta_minb3() : batch_resident_cta_minb2();
+}
+
+cudaError_t batch_launch_warp(const BatchArgs* ba, const int* perm, const BatchTable& tab, double* partials,
+                              unsigned long long* ticket, int* status, RowMode rows, cudaStream_t s) {
+  const int grid = batch_resident_blocks_rows(rows);
+  if (grid < 1) return cudaErrorInvalidConfiguration;
+  if (rows == kRowsF64)
+    k_batch<kRowsF64><<<grid, kBatchThreads, kBatchSmem, s>>>(ba, perm, tab, partials, ticket, status);
+  else
+    k_batch<kRowsFixed><<<grid, kBatchThreads, kBatchSmem, s>>>(ba, perm, tab, partials, ticket, status);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_launch_cta(int kind, const BatchArgs* ba, const int* perm, const BatchTable& tab, double* partials,
+                             unsigned long long* ticket, int* status, cudaStream_t s) {
+  return kind == kBatchCta3 ? batch_launch_cta_minb3(ba, perm, tab, kind, partials, ticket, status, s)
+                            : batch_launch_cta_minb2(ba, perm, tab, kind, partials, ticket, status, s);
+}
+
 void preload_batch_kernels() {
   load_kernel(k_batch_finalize);
   load_kernel(k_batch_stats);
+  load_kernel(k_upload);
+  load_kernel(k_set_args);
+  batch_resident_blocks_rows(kRowsF64);
+  batch_resident_blocks_rows(kRowsFixed);
+  batch_resident_cta_minb2();
+  batch_resident_cta_minb3();
 }
 
 }  // namespace perm
@@ -258,25 +331,96 @@ namespace {
 std::mutex g_batch_mu;
 std::mutex g_stats_mu;
 
-// ---- tuning table: codes per lane L for each (device, order) ----
+// ---- tuning: kernel kind and codes per thread for each (row class, device, order) ----
 struct Tune {
-  int L[kBatchNMax + 1] = {0};
+  int L[kBatchNMax + 1] = {0};     // codes per lane (warp kernel) or per thread (block kernels); 0 = untuned
+  int kind[kBatchNMax + 1] = {0};  // BatchKind; 0 = untuned
 };
-Tune g_tune_tab[2][64];  // [row mode][device]
+// row class: 0 FP64 rows, 1 exact fixed-point rows (both: warp kernel only), 2 the default arithmetic
+Tune g_tune_tab[3][64];
 
-// Tuning table of the row arithmetic currently selected (PERM_ROWS).
-Tune& tune_of(int dev) { return g_tune_tab[rows_from_env() == kRowsF64 ? 0 : 1][dev]; }
+int row_class(RowMode r) { return r == kRowsF64 ? 0 : r == kRowsFixed ? 1 : 2; }
+bool warp_only(RowMode r) { return r == kRowsF64 || r == kRowsFixed; }
+Tune& tune_of(int dev) { return g_tune_tab[row_class(rows_from_env())][dev]; }
 
-int default_L(int n) {
+// Built-in choice for an untuned order: the table perm_batch_autotune
+// measured on GB300 for orders 12..28 (kind, codes per thread); below 12 the
+// warp kernel, above 28 the block kernel with 2048 codes per thread.
+constexpr int kTunedLo = 12, kTunedHi = 28;
+constexpr int kTunedKind[kTunedHi - kTunedLo + 1] = {1, 3, 3, 3, 2, 3, 3, 3, 3, 2, 2, 2, 2, 2, 2, 2, 2};
+constexpr int kTunedL[kTunedHi - kTunedLo + 1] = {64,  32,  64,  128, 128, 128,  256,  128, 128,
+                                                 512, 512, 512, 512, 512, 1024, 2048, 1024};
+
+int default_L_warp(int n) {
   // about 16 n codes per lane keeps the O(n^2) seed near 2% of the walk
   int L = 64;
   while (L < 16 * n && L < 4096) L <<= 1;
   return L;
 }
 
-bool tuning_enabled() {
-  const char* e = std::getenv("PERM_BATCH_TUNE");
-  return !(e && e[0] == '0');
+void default_choice(int n, int& kind, int& L) {
+  if (n >= kTunedLo && n <= kTunedHi) {
+    kind = kTunedKind[n - kTunedLo];
+    L = kTunedL[n - kTunedLo];
+  } else if (n < kTunedLo) {
+    kind = kBatchWarp;
+    L = default_L_warp(n < 1 ? 1 : n);
+  } else {
+    kind = kBatchCta;
+    L = 2048;
+  }
+}
+
+struct Choice {
+  int kind[kBatchNMax + 1];
+  int L[kBatchNMax + 1];
+};
+
+Choice resolve_choice(int dev, RowMode rows) {
+  Choice c;
+  const Tune& t = g_tune_tab[row_class(rows)][dev];
+  for (int n = 0; n <= kBatchNMax; ++n) {
+    if (n >= 1 && t.kind[n] && t.L[n]) {
+      c.kind[n] = t.kind[n];
+      c.L[n] = t.L[n];
+    } else if (warp_only(rows)) {
+      c.kind[n] = kBatchWarp;
+      c.L[n] = default_L_warp(n < 1 ? 1 : n);
+    } else {
+      default_choice(n, c.kind[n], c.L[n]);
+    }
+    if (warp_only(rows) && c.kind[n] != kBatchWarp) {
+      c.kind[n] = kBatchWarp;
+      c.L[n] = default_L_warp(n < 1 ? 1 : n);
+    }
+  }
+  return c;
+}
+
+uint64_t threads_per_item(int kind) { return kind == kBatchWarp ? 32ull : (uint64_t)kBatchCtaThreads; }
+
+// Most work items one plan holds (2 GiB of partials).
+constexpr uint64_t kMaxItems = 1ull << 26;
+
+// Double the chunk length of the order contributing the most items until the
+// batch has at most max(kMaxItems, count) items, so the partials stay bounded
+// and item indices fit however large the batch.
+void bound_items(const int* cnt, Choice& c, int count) {
+  const uint64_t cap = std::max<uint64_t>(kMaxItems, (uint64_t)count);
+  for (;;) {
+    uint64_t total = 0, worst = 0;
+    int wn = -1;
+    for (int n = 1; n <= kBatchNMax; ++n) {
+      if (!cnt[n]) continue;
+      const uint64_t per_item = threads_per_item(c.kind[n]) * (uint64_t)c.L[n];
+      const uint64_t each = ((1ull << (n - 1)) + per_item - 1) / per_item;
+      const uint64_t t = (uint64_t)cnt[n] * each;
+      total += t;
+      if (each > 1 && t > worst) worst = t, wn = n;
+    }
+    if (total <= cap || wn < 0) break;
+    c.L[wn] *= 2;
+  }
 }
 
 int status_of_b(cudaError_t e) {
@@ -285,143 +429,192 @@ int status_of_b(cudaError_t e) {
   return PERM_ECUDA;
 }
 
-struct DevBuf {
-  void* p = nullptr;
-  ~DevBuf() {
-    if (p) cudaFree(p);
-  }
-};
-
 int* batch_status_word(int dev) {
   int* w = nullptr;
   return device_status_word(dev, &w) == 0 ? w : nullptr;
 }
 
-// Build the item list for `ns` with the given per-order L; matrices sorted
-// by decreasing order, each matrix's items contiguous.
-void build_items(const int* ns, int count, const int* Ltab, std::vector<BatchItem>& items, std::vector<int>& mfirst,
-                 std::vector<int>& mcount) {
-  std::vector<int> order(count);
-  for (int k = 0; k < count; ++k) order[k] = k;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ns[a] > ns[b]; });
-  items.clear();
-  mfirst.assign(count, 0);
-  mcount.assign(count, 0);
-  for (int k : order) {
-    const int n = ns[k];
-    const uint64_t total = 1ull << (n - 1);
-    const uint64_t per_item = 32ull * (uint64_t)Ltab[n];
-    mfirst[k] = (int)items.size();
-    for (uint64_t f = 0; f < total; f += per_item) {
-      BatchItem it;
-      it.matrix = (uint32_t)k;
-      it.n = (uint32_t)n;
-      it.first = f;
-      it.count = std::min(per_item, total - f);
-      items.push_back(it);
-    }
-    mcount[k] = (int)items.size() - mfirst[k];
-  }
-}
-
-// Most work items one plan holds (1.5 GiB of item list, 2 GiB of partials).
-constexpr uint64_t kMaxItems = 1ull << 26;
-
-// Chunk lengths for one batch: the tuned lengths, doubled for the order that
-// contributes the most items until the batch has at most
-// max(kMaxItems, count) items, so the item list and its partials stay bounded
-// and item indices fit in an int however large the batch.
-void plan_lengths(const int* ns, int count, const int* Ltune, int* Leff) {
-  uint64_t cnt[kBatchNMax + 1] = {0};
-  for (int k = 0; k < count; ++k) ++cnt[ns[k]];
-  for (int n = 0; n <= kBatchNMax; ++n) Leff[n] = Ltune[n] ? Ltune[n] : default_L(n < 1 ? 1 : n);
-  const uint64_t cap = std::max<uint64_t>(kMaxItems, (uint64_t)count);
-  for (;;) {
-    uint64_t total = 0, worst = 0;
-    int wn = -1;
-    for (int n = 1; n <= kBatchNMax; ++n) {
-      if (!cnt[n]) continue;
-      const uint64_t per_item = 32ull * (uint64_t)Leff[n];
-      const uint64_t each = ((1ull << (n - 1)) + per_item - 1) / per_item;
-      const uint64_t t = cnt[n] * each;
-      total += t;
-      if (each > 1 && t > worst) worst = t, wn = n;
-    }
-    if (total <= cap || wn < 0) break;
-    Leff[wn] *= 2;
-  }
-}
-
 struct Plan {
   int dev = -1;
   cudaStream_t stream = nullptr;
-  const void* ptrs = nullptr;
-  void* out = nullptr;
+  RowMode rows = kRowsPdf;
   std::vector<int> ns;
-  std::vector<int> Ls;
-  RowMode rows = kRowsFixed;
-  DevBuf items, partials, mfirst, mcount, mn, ticket;
-  int nitems = 0;
+  Choice choice{};
+  BatchTable tab{};
+  int count = 0;
+  void* args = nullptr;
+  void* perm = nullptr;
+  void* partials = nullptr;
+  void* tickets = nullptr;
   cudaGraphExec_t exec = nullptr;
+  Plan() = default;
+  Plan(const Plan&) = delete;
+  Plan& operator=(const Plan&) = delete;
   ~Plan() {
+    // cudaFree waits for any launch still using the buffers (eviction and
+    // perm_shutdown only)
     if (exec) cudaGraphExecDestroy(exec);
+    for (void* p : {args, perm, partials, tickets})
+      if (p) cudaFree(p);
   }
 };
 
-std::list<std::unique_ptr<Plan>> g_plans;  // most recent first
-constexpr size_t kMaxPlans = 8;
-
-int enqueue_batch(const double* const* ptrs, const BatchItem* d_items, int nitems, double* d_partials,
-                  const int* d_mfirst, const int* d_mcount, const int* d_mn, int count, unsigned int* d_ticket,
-                  double* out, int* status, cudaStream_t s, RowMode rows) {
-  const int grid = batch_resident_blocks_rows(rows);
-  if (grid < 1) return PERM_ECUDA;
-  cudaError_t e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned int), s);
+// Build a plan's layout, buffers (stream-ordered on s), uploaded position list
+// and graph.  Nothing here waits for the device.
+int build_plan(Plan& p, const int* ns, int count, const Choice& ch, RowMode rows, int dev, cudaStream_t s,
+               int* status) {
+  p.dev = dev;
+  p.stream = s;
+  p.rows = rows;
+  p.ns.assign(ns, ns + count);
+  p.choice = ch;
+  p.count = count;
+  int cnt[kBatchNMax + 1] = {0};
+  for (int k = 0; k < count; ++k) ++cnt[ns[k]];
+  // counting sort by decreasing order (stable within an order)
+  int start[kBatchNMax + 1] = {0}, fill[kBatchNMax + 1] = {0};
+  int pos = 0;
+  for (int n = kBatchNMax; n >= 1; --n) start[n] = fill[n] = pos, pos += cnt[n];
+  std::vector<int> perm(count);
+  for (int k = 0; k < count; ++k) perm[fill[ns[k]]++] = k;
+  BatchTable& t = p.tab;
+  std::memset(&t, 0, sizeof(t));
+  uint64_t kb[kBatchKinds] = {0, 0, 0, 0}, gb = 0;
+  for (int n = kBatchNMax; n >= 1; --n) {
+    if (!cnt[n]) continue;
+    const int kind = ch.kind[n];
+    const uint64_t per_item = threads_per_item(kind) * (uint64_t)ch.L[n];
+    const uint64_t ipm = ((1ull << (n - 1)) + per_item - 1) / per_item;
+    t.kind[n] = kind;
+    t.mstart[n] = start[n];
+    t.mcount[n] = cnt[n];
+    t.per_item[n] = per_item;
+    t.items_per_matrix[n] = ipm;
+    t.kbase[n] = kb[kind];
+    t.gbase[n] = gb;
+    kb[kind] += (uint64_t)cnt[n] * ipm;
+    gb += (uint64_t)cnt[n] * ipm;
+  }
+  for (int k = 0; k < kBatchKinds; ++k) t.kitems[k] = kb[k];
+  cudaError_t e = cudaMallocAsync(&p.args, sizeof(BatchArgs), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&p.perm, (size_t)count * sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&p.partials, (size_t)gb * 4 * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&p.tickets, kBatchKinds * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return status_of_b(e);
-  if (rows != kRowsF64)
-    k_batch<kRowsFixed><<<grid, kBatchThreads, kBatchSmem, s>>>(ptrs, d_items, nitems, d_partials, d_ticket, status);
-  else
-    k_batch<kRowsF64><<<grid, kBatchThreads, kBatchSmem, s>>>(ptrs, d_items, nitems, d_partials, d_ticket, status);
+  UploadChunk chunk;
+  for (int off = 0; off < count; off += kUploadInts) {
+    const int len = std::min(kUploadInts, count - off);
+    std::memcpy(chunk.v, perm.data() + off, (size_t)len * sizeof(int));
+    k_upload<<<1, 256, 0, s>>>((int*)p.perm + off, chunk, len);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return status_of_b(e);
-  if (out) {
-    k_batch_finalize<<<(count + 127) / 128, 128, 0, s>>>(d_partials, d_mfirst, d_mcount, d_mn, count, out);
-    e = cudaGetLastError();
+  // capture: ticket reset, the kernels that have items, finalize
+  cudaStream_t cs = nullptr;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return status_of_b(e);
+  cudaGraph_t graph = nullptr;
+  int rc = PERM_OK;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const BatchArgs* ba = (const BatchArgs*)p.args;
+    const int* dperm = (const int*)p.perm;
+    double* parts = (double*)p.partials;
+    unsigned long long* tk = (unsigned long long*)p.tickets;
+    cudaError_t el = cudaMemsetAsync(tk, 0, kBatchKinds * sizeof(unsigned long long), cs);
+    if (el == cudaSuccess && kb[kBatchWarp])
+      el = batch_launch_warp(ba, dperm, t, parts, tk + kBatchWarp, status, rows, cs);
+    if (el == cudaSuccess && kb[kBatchCta])
+      el = batch_launch_cta(kBatchCta, ba, dperm, t, parts, tk + kBatchCta, status, cs);
+    if (el == cudaSuccess && kb[kBatchCta3])
+      el = batch_launch_cta(kBatchCta3, ba, dperm, t, parts, tk + kBatchCta3, status, cs);
+    if (el == cudaSuccess) {
+      k_batch_finalize<<<(count + 127) / 128, 128, 0, cs>>>(ba, dperm, t, parts, count);
+      el = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    rc = status_of_b(el != cudaSuccess ? el : e2);
+  } else {
+    rc = status_of_b(e);
   }
-  return status_of_b(e);
+  cudaStreamDestroy(cs);
+  if (rc == PERM_OK) {
+    e = cudaGraphInstantiate(&p.exec, graph, 0);
+    if (e != cudaSuccess) rc = status_of_b(e);
+  }
+  if (graph) cudaGraphDestroy(graph);
+  return rc;
 }
 
-// Time one candidate L for order n on a synthetic batch (blocking).
-int time_candidate(int n, int L, const double* const* d_ptrs, int m, double* ms_out) {
+bool same_choice(const Choice& a, const Choice& b, const int* cnt) {
+  for (int n = 1; n <= kBatchNMax; ++n)
+    if (cnt[n] && (a.kind[n] != b.kind[n] || a.L[n] != b.L[n])) return false;
+  return true;
+}
+
+std::list<std::unique_ptr<Plan>> g_plans;  // most recent first
+constexpr size_t kMaxPlans = 8;
+std::atomic<int> g_plans_built{0};         // plans built by batch calls (not by tuning)
+
+// Find or build the plan for (device, stream, row arithmetic, orders, tuning);
+// the caller holds g_batch_mu.
+int plan_for(const int* ns, int count, int dev, cudaStream_t s, int* status, const Choice* forced, Plan** out) {
+  const RowMode rows = rows_from_env();
+  int cnt[kBatchNMax + 1] = {0};
+  for (int k = 0; k < count; ++k) ++cnt[ns[k]];
+  Choice ch = forced ? *forced : resolve_choice(dev, rows);
+  bound_items(cnt, ch, count);
+  for (auto it = g_plans.begin(); it != g_plans.end(); ++it) {
+    Plan* p = it->get();
+    if (p->dev == dev && p->stream == s && p->rows == rows && p->count == count &&
+        std::memcmp(p->ns.data(), ns, (size_t)count * sizeof(int)) == 0 && same_choice(p->choice, ch, cnt)) {
+      g_plans.splice(g_plans.begin(), g_plans, it);
+      *out = p;
+      return PERM_OK;
+    }
+  }
+  auto np = std::make_unique<Plan>();
+  int rc = build_plan(*np, ns, count, ch, rows, dev, s, status);
+  if (rc) return rc;
+  ++g_plans_built;
+  g_plans.push_front(std::move(np));
+  while (g_plans.size() > kMaxPlans) g_plans.pop_back();
+  *out = g_plans.front().get();
+  return PERM_OK;
+}
+
+int launch_plan(Plan* p, const double* const* ptrs, double* out, cudaStream_t s) {
+  k_set_args<<<1, 1, 0, s>>>((BatchArgs*)p->args, ptrs, out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return status_of_b(e);
+  return status_of_b(cudaGraphLaunch(p->exec, s));
+}
+
+// ---- tuning (blocking; perm_batch_autotune only) ----
+// Time one (kind, L) for order n on a synthetic batch of m copies of one
+// matrix; returns the best of two timed launches after a warm-up.
+int time_choice(int n, int kind, int L, int m, const double* const* d_ptrs, double* d_out, int dev, int* status,
+                cudaStream_t s, double* ms_out) {
   std::vector<int> ns(m, n);
-  int Ltab[kBatchNMax + 1];
-  for (int k = 0; k <= kBatchNMax; ++k) Ltab[k] = L;
-  std::vector<BatchItem> items;
-  std::vector<int> mf, mc;
-  build_items(ns.data(), m, Ltab, items, mf, mc);
-  DevBuf di, dp, dt;
-  if (cudaMalloc(&di.p, items.size() * sizeof(BatchItem)) != cudaSuccess) return PERM_ENOMEM;
-  if (cudaMalloc(&dp.p, items.size() * 4 * sizeof(double)) != cudaSuccess) return PERM_ENOMEM;
-  if (cudaMalloc(&dt.p, sizeof(unsigned int)) != cudaSuccess) return PERM_ENOMEM;
-  cudaMemcpy(di.p, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
-  int dev = 0;
-  cudaGetDevice(&dev);
-  int* status = batch_status_word(dev);
+  Choice ch = resolve_choice(dev, rows_from_env());
+  ch.kind[n] = kind;
+  ch.L[n] = L;
+  Plan p;
+  int rc = build_plan(p, ns.data(), m, ch, rows_from_env(), dev, s, status);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
-  int rc = PERM_OK;
   for (int rep = 0; rep < 3 && rc == PERM_OK; ++rep) {
-    cudaEventRecord(e0, nullptr);
-    rc = enqueue_batch(d_ptrs, (BatchItem*)di.p, (int)items.size(), (double*)dp.p, nullptr, nullptr, nullptr, 0,
-                       (unsigned int*)dt.p, nullptr, status, nullptr, rows_from_env());
-    cudaEventRecord(e1, nullptr);
+    cudaEventRecord(e0, s);
+    rc = launch_plan(&p, d_ptrs, d_out, s);
+    cudaEventRecord(e1, s);
     if (cudaEventSynchronize(e1) != cudaSuccess) rc = PERM_ECUDA;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     if (rep > 0 && ms < best) best = ms;
   }
+  cudaStreamSynchronize(s);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   *ms_out = best;
@@ -429,11 +622,7 @@ int time_candidate(int n, int L, const double* const* d_ptrs, int m, double* ms_
 }
 
 int autotune_order(int dev, int n) {
-  if (tune_of(dev).L[n]) return PERM_OK;
-  if (!tuning_enabled() || n < 4) {
-    tune_of(dev).L[n] = default_L(n);
-    return PERM_OK;
-  }
+  const RowMode rows = rows_from_env();
   // synthetic matrix (fixed linear congruential values in [-1, 1)), replicated
   // so the batch carries at least 2^24 codes
   std::vector<double> h(2 * n * n);
@@ -443,24 +632,43 @@ int autotune_order(int dev, int n) {
     v = (double)(int64_t)(st >> 11) / (double)(1ull << 52) - 1.0;
   }
   const uint64_t per = 1ull << (n - 1);
-  int m = (int)std::max<uint64_t>(1, (1ull << 24) / per);
-  DevBuf dA, dptrs;
-  if (cudaMalloc(&dA.p, h.size() * sizeof(double)) != cudaSuccess) return PERM_ENOMEM;
-  if (cudaMalloc(&dptrs.p, (size_t)m * sizeof(double*)) != cudaSuccess) return PERM_ENOMEM;
-  cudaMemcpy(dA.p, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
-  std::vector<const double*> hp(m, (const double*)dA.p);
-  cudaMemcpy(dptrs.p, hp.data(), (size_t)m * sizeof(double*), cudaMemcpyHostToDevice);
-  double best_rate = 0.0;
-  int bestL = default_L(n);
-  for (int L = 16; L <= 8192; L <<= 1) {
-    if (32ull * L > per * 4 && L > 16) break;  // items much larger than a matrix: no new candidates
-    double ms = 0;
-    int rc = time_candidate(n, L, (const double* const*)dptrs.p, m, &ms);
-    if (rc) return rc;
-    const double rate = (double)per * m / ms;
-    if (rate > best_rate * 1.01) best_rate = rate, bestL = L;
+  const int m = (int)std::max<uint64_t>(1, (1ull << 24) / per);
+  int* status = batch_status_word(dev);
+  if (!status) return PERM_ENOMEM;
+  void *dA = nullptr, *dptrs = nullptr, *dout = nullptr;
+  cudaStream_t s = nullptr;
+  int rc = PERM_OK;
+  if (cudaMalloc(&dA, h.size() * sizeof(double)) != cudaSuccess || cudaMalloc(&dptrs, (size_t)m * sizeof(double*)) != cudaSuccess ||
+      cudaMalloc(&dout, (size_t)m * 2 * sizeof(double)) != cudaSuccess)
+    rc = PERM_ENOMEM;
+  if (rc == PERM_OK && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) rc = PERM_ECUDA;
+  if (rc == PERM_OK) {
+    cudaMemcpy(dA, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
+    std::vector<const double*> hp(m, (const double*)dA);
+    cudaMemcpy(dptrs, hp.data(), (size_t)m * sizeof(double*), cudaMemcpyHostToDevice);
   }
-  tune_of(dev).L[n] = bestL;
+  double best_rate = 0.0;
+  int best_kind = kBatchWarp, best_L = default_L_warp(n);
+  if (!warp_only(rows)) default_choice(n, best_kind, best_L);
+  const int kinds[3] = {kBatchWarp, kBatchCta, kBatchCta3};
+  for (int ki = 0; ki < 3 && rc == PERM_OK; ++ki) {
+    const int kind = kinds[ki];
+    if (kind != kBatchWarp && warp_only(rows)) continue;
+    for (int L = 16; L <= 8192 && rc == PERM_OK; L <<= 1) {
+      if (threads_per_item(kind) * (uint64_t)L > per * 4 && L > 16) break;  // items far larger than a matrix
+      double ms = 0;
+      rc = time_choice(n, kind, L, m, (const double* const*)dptrs, (double*)dout, dev, status, s, &ms);
+      if (rc) break;
+      const double rate = (double)per * m / ms;
+      if (rate > best_rate * 1.01) best_rate = rate, best_kind = kind, best_L = L;
+    }
+  }
+  if (s) cudaStreamDestroy(s);
+  for (void* p : {dA, dptrs, dout})
+    if (p) cudaFree(p);
+  if (rc) return rc;
+  tune_of(dev).kind[n] = best_kind;
+  tune_of(dev).L[n] = best_L;
   return PERM_OK;
 }
 
@@ -468,23 +676,28 @@ int autotune_order(int dev, int n) {
 
 extern "C" {
 
-int perm_batch_tuning(int device, int* L, int set) {
-  if (!L) return PERM_ENULL;
+int perm_batch_tuning(int device, int* L, int* kind, int set) {
+  if (!L || !kind) return PERM_ENULL;
   if (device < 0 || device >= 64) return PERM_EINVAL;
   if (set) {
-    // every entry 0 (not tuned) or a power of two in 16 .. 2^24 codes per lane
-    for (int n = 0; n <= kBatchNMax; ++n) {
-      const int v = L[n];
+    // every entry 0 (untuned) or a power of two in 16 .. 2^24 codes, with a kind 1..3
+    for (int n = 1; n <= kBatchNMax; ++n) {
+      const int v = L[n], k = kind[n];
+      if ((v == 0) != (k == 0)) return PERM_EINVAL;
       if (v != 0 && (v < 16 || v > (1 << 24) || (v & (v - 1)) != 0)) return PERM_EINVAL;
+      if (k < 0 || k >= kBatchKinds) return PERM_EINVAL;
     }
   }
   std::lock_guard<std::mutex> lk(g_batch_mu);
-  Tune& t = g_tune_tab[rows_from_env() == kRowsF64 ? 0 : 1][device];
+  Tune& t = g_tune_tab[row_class(rows_from_env())][device];
   for (int n = 0; n <= kBatchNMax; ++n) {
-    if (set)
+    if (set) {
       t.L[n] = n == 0 ? 0 : L[n];
-    else
+      t.kind[n] = n == 0 ? 0 : kind[n];
+    } else {
       L[n] = t.L[n];
+      kind[n] = t.kind[n];
+    }
   }
   return PERM_OK;
 }
@@ -501,15 +714,13 @@ int perm_batch_autotune(int n_lo, int n_hi) {
   ensure_kernels_loaded();
   std::lock_guard<std::mutex> lk(g_batch_mu);
   for (int n = n_lo; n <= n_hi; ++n) {
-    tune_of(dev).L[n] = 0;
     int rc = autotune_order(dev, n);
     if (rc) return rc;
   }
   return PERM_OK;
 }
 
-static int batch_run(const double* const* ptrs, const int* ns, int count, double* out, void* stream,
-                     const int** dev_ns) {
+static int batch_run(const double* const* ptrs, const int* ns, int count, double* out, void* stream, double* stats) {
   if (!ptrs || !ns || !out) return PERM_ENULL;
   if (count < 1) return PERM_EINVAL;
   for (int k = 0; k < count; ++k)
@@ -525,95 +736,27 @@ static int batch_run(const double* const* ptrs, const int* ns, int count, double
   std::lock_guard<std::mutex> lk(g_batch_mu);
   int* status = batch_status_word(dev);
   if (!status) return PERM_ENOMEM;
-  if (batch_resident_blocks() < 1) return PERM_ECUDA;
-
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  cudaStreamIsCapturing(s, &cap);
-  bool seen[kBatchNMax + 1] = {false};
-  for (int k = 0; k < count; ++k) seen[ns[k]] = true;
-  for (int n = 1; n <= kBatchNMax; ++n) {
-    if (!seen[n] || tune_of(dev).L[n]) continue;
-    if (cap != cudaStreamCaptureStatusNone) {
-      tune_of(dev).L[n] = default_L(n);  // no timing while the caller captures
-    } else {
-      int rc = autotune_order(dev, n);
-      if (rc) return rc;
-    }
-  }
-
-  // plan lookup
   Plan* plan = nullptr;
-  for (auto it = g_plans.begin(); it != g_plans.end(); ++it) {
-    Plan* p = it->get();
-    if (p->dev == dev && p->stream == s && p->ptrs == (const void*)ptrs && p->out == (void*)out &&
-        p->rows == rows_from_env() &&
-        (int)p->ns.size() == count && std::memcmp(p->ns.data(), ns, count * sizeof(int)) == 0) {
-      bool sameL = true;
-      for (int n = 1; n <= kBatchNMax; ++n)
-        if (seen[n] && p->Ls[n] != tune_of(dev).L[n]) sameL = false;
-      if (!sameL) break;
-      g_plans.splice(g_plans.begin(), g_plans, it);
-      plan = p;
-      break;
-    }
+  int rc = plan_for(ns, count, dev, s, status, nullptr, &plan);
+  if (rc) return rc;
+  rc = launch_plan(plan, ptrs, out, s);
+  if (rc || !stats) return rc;
+  StatsParams sp;
+  for (int n = 0; n <= kBatchNMax; ++n) {
+    double f = 1.0;
+    for (int t = 2; t <= n; ++t) f *= (double)t;
+    sp.inv_sqrt_fact[n] = 1.0 / std::sqrt(f);
   }
-  if (!plan) {
-    auto np = std::make_unique<Plan>();
-    np->dev = dev;
-    np->stream = s;
-    np->ptrs = ptrs;
-    np->out = out;
-    np->ns.assign(ns, ns + count);
-    np->rows = rows_from_env();
-    np->Ls.assign(tune_of(dev).L, tune_of(dev).L + kBatchNMax + 1);
-    std::vector<BatchItem> items;
-    std::vector<int> mf, mc;
-    int Leff[kBatchNMax + 1];
-    plan_lengths(ns, count, tune_of(dev).L, Leff);
-    build_items(ns, count, Leff, items, mf, mc);
-    if (items.size() > (size_t)std::max<uint64_t>(kMaxItems, (uint64_t)count)) return PERM_ENOMEM;
-    np->nitems = (int)items.size();
-    cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc(&np->items.p, items.size() * sizeof(BatchItem));
-    if (e == cudaSuccess) e = cudaMalloc(&np->partials.p, items.size() * 4 * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&np->mfirst.p, count * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&np->mcount.p, count * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&np->mn.p, count * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&np->ticket.p, sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMemcpy(np->items.p, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(np->mfirst.p, mf.data(), count * sizeof(int), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(np->mcount.p, mc.data(), count * sizeof(int), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(np->mn.p, ns, count * sizeof(int), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return status_of_b(e);
-    // capture ticket reset + persistent kernel + finalize into a graph
-    cudaStream_t cs = nullptr;
-    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return status_of_b(e);
-    cudaGraph_t graph = nullptr;
-    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    int rc = PERM_OK;
-    if (e == cudaSuccess) {
-      rc = enqueue_batch(ptrs, (BatchItem*)np->items.p, np->nitems, (double*)np->partials.p, (int*)np->mfirst.p,
-                         (int*)np->mcount.p, (int*)np->mn.p, count, (unsigned int*)np->ticket.p, out, status, cs,
-                         np->rows);
-      cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
-      if (rc == PERM_OK && e2 != cudaSuccess) rc = status_of_b(e2);
-    } else {
-      rc = status_of_b(e);
-    }
-    cudaStreamDestroy(cs);
-    if (rc == PERM_OK) {
-      e = cudaGraphInstantiate(&np->exec, graph, 0);
-      if (e != cudaSuccess) rc = status_of_b(e);
-    }
-    if (graph) cudaGraphDestroy(graph);
-    if (rc) return rc;
-    g_plans.push_front(std::move(np));
-    while (g_plans.size() > kMaxPlans) g_plans.pop_back();
-    plan = g_plans.front().get();
-  }
-  if (dev_ns) *dev_ns = (const int*)plan->mn.p;
-  return status_of_b(cudaGraphLaunch(plan->exec, s));
+  for (int j = 0; j < kStatsEdges; ++j) sp.edges[j] = std::pow(10.0, -4.0 + (double)j / 16.0);
+  k_batch_stats<<<kBatchNMax + 1, 256, 0, s>>>((const BatchArgs*)plan->args, (const int*)plan->perm, plan->tab, sp,
+                                               stats);
+  return status_of_b(cudaGetLastError());
+}
+
+int perm_batch_plans(int* built) {
+  if (!built) return PERM_ENULL;
+  *built = g_plans_built.load();
+  return PERM_OK;
 }
 
 int perm_batch(const double* const* ptrs, const int* ns, int count, double* out, void* stream) {
@@ -624,19 +767,8 @@ int perm_batch(const double* const* ptrs, const int* ns, int count, double* out,
 int perm_batch_stats(const double* const* ptrs, const int* ns, int count, double* out, double* stats, void* stream) {
   TraceRange trace("perm_batch_stats");
   if (!stats) return PERM_ENULL;
-  const int* d_ns = nullptr;
   std::lock_guard<std::mutex> lk(g_stats_mu);
-  int rc = batch_run(ptrs, ns, count, out, stream, &d_ns);
-  if (rc) return rc;
-  StatsParams sp;
-  for (int n = 0; n <= kBatchNMax; ++n) {
-    double f = 1.0;
-    for (int t = 2; t <= n; ++t) f *= (double)t;
-    sp.inv_sqrt_fact[n] = 1.0 / std::sqrt(f);
-  }
-  for (int j = 0; j < kStatsEdges; ++j) sp.edges[j] = std::pow(10.0, -4.0 + (double)j / 16.0);
-  k_batch_stats<<<kBatchNMax + 1, 256, 0, (cudaStream_t)stream>>>(out, d_ns, count, sp, stats);
-  return status_of_b(cudaGetLastError());
+  return batch_run(ptrs, ns, count, out, stream, stats);
 }
 
 }  // extern "C"

@@ -1,0 +1,13 @@
+// Block-per-item batch kernel, variant allowing 3 blocks per SM (batch_cta.cuh).
+#include "batch_cta.cuh"
+
+namespace perm {
+
+cudaError_t batch_launch_cta_minb3(const BatchArgs* ba, const int* perm, const BatchTable& tab, int kind,
+                                   double* partials, unsigned long long* ticket, int* status, cudaStream_t s) {
+  return CtaKernel<3>::launch(ba, perm, tab, kind, partials, ticket, status, s);
+}
+
+int batch_resident_cta_minb3() { return CtaKernel<3>::resident(); }
+
+}  // namespace perm

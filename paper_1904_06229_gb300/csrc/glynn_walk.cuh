@@ -245,7 +245,16 @@ __device__ __forceinline__ void stage(const double* __restrict__ A, double* sA, 
 // Block-level fixed-order reduction of per-thread dd sums; thread 0 writes
 // (or adds into) this block's slot of `partials`.
 template <bool CPLX>
+__device__ __forceinline__ void block_store_to(dd accr, dd acci, dd* sRed, double* o, int accumulate);
+
+template <bool CPLX>
 __device__ __forceinline__ void block_store(dd accr, dd acci, dd* sRed, double* partials, int accumulate) {
+  block_store_to<CPLX>(accr, acci, sRed, partials + (size_t)blockIdx.x * (CPLX ? 4 : 2), accumulate);
+}
+
+// The same reduction, written to (or added into) the partial at o.
+template <bool CPLX>
+__device__ __forceinline__ void block_store_to(dd accr, dd acci, dd* sRed, double* o, int accumulate) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   accr = dd_warp_sum(accr);
   if (CPLX) acci = dd_warp_sum(acci);
@@ -261,7 +270,6 @@ __device__ __forceinline__ void block_store(dd accr, dd acci, dd* sRed, double* 
       tr = dd_add(tr, sRed[2 * w]);
       ti = dd_add(ti, sRed[2 * w + 1]);
     }
-    double* o = partials + (size_t)blockIdx.x * (CPLX ? 4 : 2);
     if (accumulate) {
       tr = dd_add(tr, dd{o[0], o[1]});
       if (CPLX) ti = dd_add(ti, dd{o[2], o[3]});

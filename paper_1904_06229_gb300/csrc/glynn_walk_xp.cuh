@@ -447,9 +447,8 @@ __device__ __forceinline__ void pdf_seed(P4 (&v)[kPairs<N>], const longlong2* __
 // alignment a (2^kXpAlignLog, or the power of two at or above the length when
 // that is smaller, so that short launches still use every thread), so every
 // thread starts at a code congruent to `first` modulo a.
-__device__ __forceinline__ void thread_range_congruent(uint64_t first, uint64_t count, uint64_t& r, uint64_t& end) {
-  const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
-  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void range_congruent(uint64_t first, uint64_t count, uint64_t T, uint64_t g, uint64_t& r,
+                                                uint64_t& end) {
   uint64_t L = (count + T - 1) / T;
   uint64_t kA = 1ull << kXpAlignLog;
   while (kA > 1 && (kA >> 1) >= L) kA >>= 1;
@@ -457,6 +456,12 @@ __device__ __forceinline__ void thread_range_congruent(uint64_t first, uint64_t 
   const uint64_t s = g * L;
   r = first + (s < count ? s : count);
   end = first + (s + L < count ? s + L : count);
+}
+
+// The whole launch's threads over [first, first + count).
+__device__ __forceinline__ void thread_range_congruent(uint64_t first, uint64_t count, uint64_t& r, uint64_t& end) {
+  range_congruent(first, count, (uint64_t)gridDim.x * blockDim.x, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                  r, end);
 }
 
 // Add one term (-1)^r prod_i u_i, rebuilt as FP64, into the run sums.

@@ -123,17 +123,54 @@ cudaError_t mod_launch_hi(int n, const int8_t* A, const ModConsts& c, uint64_t c
                           cudaStream_t s);
 
 // ---- batch path ----
-struct BatchItem {
-  uint32_t matrix;   // index into the matrix list
-  uint32_t n;        // order
-  uint64_t first;    // first code of this item
-  uint64_t count;    // codes in this item (per warp: 32 lanes share it)
+constexpr int kBatchNMax = 32;  // largest order perm_batch accepts
+
+// Kernel that walks the matrices of one order.
+enum BatchKind : int {
+  kBatchNone = 0,  // no matrices of this order
+  kBatchWarp = 1,  // one warp per item, exact fixed-point rows (batch.cu: k_batch)
+  kBatchCta = 2,   // one block of 128 threads per item, packed double-float walk, 255 registers (batch_cta.cu)
+  kBatchCta3 = 3,  // the same with a 168-register cap (three blocks per SM)
 };
-cudaError_t batch_launch(const double* const* ptrs, const BatchItem* items, int nitems, const int* item_offsets,
-                         const int* nmat_items, int count, double* item_partials, unsigned int* ticket,
-                         double* out, int grid, int* status, cudaStream_t stream);
-int batch_resident_blocks();
-int batch_resident_blocks_rows(RowMode rows);
+constexpr int kBatchKinds = 4;
+constexpr int kBatchCtaThreads = 128;  // threads of a block-per-item kernel
+
+// Where the pointers of one call live: set by a one-thread kernel before each
+// graph launch, so a cached plan serves any matrices and output of its shape.
+struct BatchArgs {
+  const double* const* ptrs;  // device array of `count` device matrix pointers
+  double* out;                // 2 * count doubles
+};
+
+// Per-order layout of a batch (a kernel parameter).  Matrices are grouped by
+// order, largest first (perm: positions -> matrix indices); the items of an
+// order are (matrix slot, code chunk) pairs numbered slot-major.  Item
+// partials are numbered by gbase; each kernel kind numbers its own items from
+// 0 by kbase (its ticket space).
+struct BatchTable {
+  int kind[kBatchNMax + 1];
+  int mstart[kBatchNMax + 1];  // first position of the order's matrices in perm
+  int mcount[kBatchNMax + 1];  // matrices of the order
+  uint64_t per_item[kBatchNMax + 1];          // codes per item
+  uint64_t items_per_matrix[kBatchNMax + 1];  // ceil(2^(n-1) / per_item)
+  uint64_t kbase[kBatchNMax + 1];             // first ticket of the order in its kernel
+  uint64_t gbase[kBatchNMax + 1];             // first item partial of the order
+  uint64_t kitems[kBatchKinds];               // tickets of each kernel kind
+};
+
+cudaError_t batch_launch_warp(const BatchArgs* ba, const int* perm, const BatchTable& tab, double* partials,
+                              unsigned long long* ticket, int* status, RowMode rows, cudaStream_t s);
+cudaError_t batch_launch_cta(int kind, const BatchArgs* ba, const int* perm, const BatchTable& tab, double* partials,
+                             unsigned long long* ticket, int* status, cudaStream_t s);
+int batch_resident_blocks_rows(RowMode rows);   // warp kernel
+int batch_resident_blocks_cta(int kind);        // block-per-item kernels
+// the two block-per-item variants (batch_cta2.cu, batch_cta3.cu)
+cudaError_t batch_launch_cta_minb2(const BatchArgs* ba, const int* perm, const BatchTable& tab, int kind,
+                                   double* partials, unsigned long long* ticket, int* status, cudaStream_t s);
+cudaError_t batch_launch_cta_minb3(const BatchArgs* ba, const int* perm, const BatchTable& tab, int kind,
+                                   double* partials, unsigned long long* ticket, int* status, cudaStream_t s);
+int batch_resident_cta_minb2();
+int batch_resident_cta_minb3();
 
 // Per-device status word (device int, OR-ed by kernels; read and cleared by
 // perm_last_status).  Allocated on first use.

@@ -47,6 +47,7 @@ EXPORTS = [
     "perm_batch_stats",
     "perm_batch_autotune",
     "perm_batch_tuning",
+    "perm_batch_plans",
     "perm_mod01",
     "perm_crt",
     "perm_default_primes",
@@ -94,7 +95,8 @@ def load(path: Optional[str] = None):
             "perm_batch": [vp, vp, i, vp, vp],
             "perm_batch_stats": [vp, vp, i, vp, vp, vp],
             "perm_batch_autotune": [i, i],
-            "perm_batch_tuning": [i, vp, i],
+            "perm_batch_tuning": [i, vp, vp, i],
+            "perm_batch_plans": [vp],
             "perm_mod01": [vp, i, vp, vp, vp],
             "perm_crt": [vp, vp, i, vp],
             "perm_default_primes": [vp],
@@ -281,11 +283,24 @@ def perm_sparse_partition(A) -> tuple:
     return [int(v) for v in block], int(count.value)
 
 
-def perm_batch(mats: Sequence[torch.Tensor], out: Optional[torch.Tensor] = None, stream=None,
-               ptrs: Optional[torch.Tensor] = None) -> torch.Tensor:
-    """Permanents of a list of complex128 CUDA matrices -> (count, 2) float64.
+def _launch_stream(dev, stream):
+    """(raw handle, torch stream) of the stream a call runs on."""
+    if stream is None:
+        st = torch.cuda.current_stream(dev)
+    elif hasattr(stream, "cuda_stream"):
+        st = stream
+    else:
+        st = torch.cuda.ExternalStream(int(stream), device=dev)
+    return int(st.cuda_stream), st
 
-    `ptrs` may pass a prebuilt device int64 tensor of the matrices' addresses."""
+
+def _batch_args(mats, out, ptrs, stream):
+    """Orders, pointer tensor, output and launch stream of a batch call.  A
+    pointer array or output made here is created on the current stream; when
+    the call runs on another stream, that stream first waits for the current
+    one (the copy of the pointers, the caller's matrices) and the temporaries
+    are recorded on it, so the caching allocator cannot hand their memory to
+    other work before the batch has read them."""
     count = len(mats)
     if count == 0:
         raise ValueError("empty batch")
@@ -294,12 +309,29 @@ def perm_batch(mats: Sequence[torch.Tensor], out: Optional[torch.Tensor] = None,
     for m in mats:
         if m.dtype != torch.complex128 or not m.is_contiguous() or m.device != dev:
             raise TypeError("contiguous complex128 matrices on one device expected")
+    made = []
     if ptrs is None:
         ptrs = torch.tensor([m.data_ptr() for m in mats], dtype=torch.int64).to(dev)
+        made.append(ptrs)
     if out is None:
         out = torch.empty((count, 2), dtype=torch.float64, device=dev)
-    _check(load().perm_batch(_dptr(ptrs), ctypes.addressof(ns), count, _dptr(out), _stream(mats[0], stream)),
-           "perm_batch")
+        made.append(out)
+    raw, st = _launch_stream(dev, stream)
+    cur = torch.cuda.current_stream(dev)
+    if st.cuda_stream != cur.cuda_stream:
+        st.wait_stream(cur)
+        for t in made:
+            t.record_stream(st)
+    return ns, ptrs, out, raw, st, made
+
+
+def perm_batch(mats: Sequence[torch.Tensor], out: Optional[torch.Tensor] = None, stream=None,
+               ptrs: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Permanents of a list of complex128 CUDA matrices -> (count, 2) float64.
+
+    `ptrs` may pass a prebuilt device int64 tensor of the matrices' addresses."""
+    ns, ptrs, out, raw, _, _ = _batch_args(mats, out, ptrs, stream)
+    _check(load().perm_batch(_dptr(ptrs), ctypes.addressof(ns), len(mats), _dptr(out), raw), "perm_batch")
     return out
 
 
@@ -310,42 +342,48 @@ def perm_batch_stats(mats: Sequence[torch.Tensor], out: Optional[torch.Tensor] =
                      stats: Optional[torch.Tensor] = None, stream=None, ptrs: Optional[torch.Tensor] = None):
     """perm_batch plus the per-order statistics of X = |per| / sqrt(n!) ->
     (out (count, 2), stats (33, PERM_STATS_STRIDE)); see include/perm.h."""
-    count = len(mats)
-    if count == 0:
-        raise ValueError("empty batch")
-    dev = mats[0].device
-    ns = (ctypes.c_int * count)(*[_square(m) for m in mats])
-    for m in mats:
-        if m.dtype != torch.complex128 or not m.is_contiguous() or m.device != dev:
-            raise TypeError("contiguous complex128 matrices on one device expected")
-    if ptrs is None:
-        ptrs = torch.tensor([m.data_ptr() for m in mats], dtype=torch.int64).to(dev)
-    if out is None:
-        out = torch.empty((count, 2), dtype=torch.float64, device=dev)
+    ns, ptrs, out, raw, st, _ = _batch_args(mats, out, ptrs, stream)
     if stats is None:
-        stats = torch.empty((33, PERM_STATS_STRIDE), dtype=torch.float64, device=dev)
-    _check(load().perm_batch_stats(_dptr(ptrs), ctypes.addressof(ns), count, _dptr(out), _dptr(stats),
-                                   _stream(mats[0], stream)), "perm_batch_stats")
+        stats = torch.empty((33, PERM_STATS_STRIDE), dtype=torch.float64, device=mats[0].device)
+        if st.cuda_stream != torch.cuda.current_stream(mats[0].device).cuda_stream:
+            stats.record_stream(st)
+    _check(load().perm_batch_stats(_dptr(ptrs), ctypes.addressof(ns), len(mats), _dptr(out), _dptr(stats), raw),
+           "perm_batch_stats")
     return out, stats
+
+
+def perm_batch_plans() -> int:
+    """Number of batch plans (graphs) this process has built so far."""
+    v = ctypes.c_int(0)
+    _check(load().perm_batch_plans(ctypes.addressof(v)), "perm_batch_plans")
+    return int(v.value)
 
 
 def perm_batch_autotune(n_lo: int, n_hi: int) -> None:
     _check(load().perm_batch_autotune(int(n_lo), int(n_hi)), "perm_batch_autotune")
 
 
-def perm_batch_tuning(device: int, L: Optional[Sequence[int]] = None) -> list:
-    """Read the batch tuning table of `device` (L is None), or replace it with
-    L (33 ints, L[n] codes per lane for order n, 0 = untuned); returns the
-    table in force afterwards."""
+BATCH_KINDS = {"warp": 1, "cta": 2, "cta3": 3}
+
+
+def perm_batch_tuning(device: int, L: Optional[Sequence[int]] = None, kind: Optional[Sequence[int]] = None):
+    """Read the batch tuning table of `device` (L and kind None), or replace it
+    (33 ints each: for order n, L[n] codes per thread and kind[n] the kernel,
+    1 warp per item, 2 block per item, 3 block per item with three blocks per
+    SM; 0 = untuned); returns the table in force afterwards as (L, kind)."""
     buf = (ctypes.c_int * 33)()
-    if L is not None:
-        if len(L) != 33:
-            raise ValueError("33 entries expected (orders 0..32)")
-        for k, v in enumerate(L):
-            buf[k] = int(v)
-        _check(load().perm_batch_tuning(int(device), ctypes.addressof(buf), 1), "perm_batch_tuning")
-    _check(load().perm_batch_tuning(int(device), ctypes.addressof(buf), 0), "perm_batch_tuning")
-    return [int(v) for v in buf]
+    kbuf = (ctypes.c_int * 33)()
+    if L is not None or kind is not None:
+        if L is None or kind is None or len(L) != 33 or len(kind) != 33:
+            raise ValueError("33 entries expected in both L and kind (orders 0..32)")
+        for k in range(33):
+            buf[k] = int(L[k])
+            kbuf[k] = int(kind[k])
+        _check(load().perm_batch_tuning(int(device), ctypes.addressof(buf), ctypes.addressof(kbuf), 1),
+               "perm_batch_tuning")
+    _check(load().perm_batch_tuning(int(device), ctypes.addressof(buf), ctypes.addressof(kbuf), 0),
+           "perm_batch_tuning")
+    return [int(v) for v in buf], [int(v) for v in kbuf]
 
 
 def save_batch_tuning(path: str, device: int = 0, name: Optional[str] = None) -> None:
@@ -358,7 +396,8 @@ def save_batch_tuning(path: str, device: int = 0, name: Optional[str] = None) ->
     if os.path.exists(path):
         with open(path) as f:
             data = json.load(f)
-    data[key] = perm_batch_tuning(device)
+    L, kind = perm_batch_tuning(device)
+    data[key] = {"L": L, "kind": kind}
     tmp = path + ".tmp"
     with open(tmp, "w") as f:
         json.dump(data, f, indent=1, sort_keys=True)
@@ -377,7 +416,7 @@ def load_batch_tuning(path: str, device: int = 0, name: Optional[str] = None) ->
         data = json.load(f)
     if key not in data:
         return False
-    perm_batch_tuning(device, data[key])
+    perm_batch_tuning(device, data[key]["L"], data[key]["kind"])
     return True
 
 

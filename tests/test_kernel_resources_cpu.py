@@ -1,9 +1,10 @@
 """Register and spill budget of the hot kernels, read from ptxas's resource
-report at compile time (no GPU): the measured rates depend on the n = 40
-walk, the batch kernel and the modular kernel at the benchmarked orders
-staying (nearly) free of register spills: none for the walks and the modular
-kernel, at most 8 bytes for the batch kernel (4 bytes in the measured
-version, which holds every order up to 32 in one kernel)."""
+report at compile time (no GPU): the measured rates depend on the default
+packed walk at n = 40 and 48, the block-per-item batch kernel, the warp batch
+kernel and the modular kernel at the benchmarked orders staying (nearly) free
+of register spills: none for the walks, the block batch kernel and the
+modular kernel, at most 8 bytes for the warp batch kernel (which holds every
+order up to 32 in one kernel)."""
 import os
 import re
 import shutil
@@ -19,7 +20,10 @@ INC = os.path.join(ROOT, "include")
 
 # (source file, mangled-name fragment of the kernel, what it is, spill bytes allowed)
 CASES = [
-    ("walk_fx_c128_f64_hi.cu", "k_walk_fxILi40ELb1ELi0E", "n = 40 complex walk (bench)", 0),
+    ("walk_pdf_c128_hi.cu", "k_walk_xpILi40ELb0E", "n = 40 packed walk (bench)", 0),
+    ("walk_pdf_c128_hi.cu", "k_walk_xpILi48ELb0E", "n = 48 packed walk", 0),
+    ("batch_cta2.cu", "k_batch_ctaILi2E", "block-per-item batch kernel", 0),
+    ("walk_fx_c128_f64_hi.cu", "k_walk_fxILi40ELb1ELi0E", "n = 40 fixed-point walk", 0),
     ("walk_fx_c128_f64_hi.cu", "k_walk_fxILi36ELb1ELi0E", "n = 36 complex walk", 0),
     ("batch.cu", "k_batchILi1E", "batch kernel, fixed-point rows", 8),
     ("mod_lo.cu", "k_modILi30E", "exact 0-1, n = 30", 0),
