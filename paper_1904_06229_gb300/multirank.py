@@ -54,3 +54,24 @@ def combine_partials(partials: Sequence[Sequence[Sequence[float]]], n: int) -> c
             im = dd_add(im, (float(p[2]), float(p[3])))
     s = 2.0 if (n - 1) % 2 == 0 else -2.0
     return complex(s * (re[0] + re[1]), s * (im[0] + im[1]))
+
+
+def shard_batch(ns: Sequence[int], world: int) -> List[List[int]]:
+    """Deal the matrices of a batch to `world` ranks so that each rank's work,
+    the sum of 2^(n-1) Gray codes over its matrices, is as even as a greedy
+    deal makes it: matrices in decreasing order of cost (ties by index), each
+    to the rank with the least work so far (ties to the lowest rank).  Batch
+    items share nothing, so the ranks run their shards with no exchange at
+    all; returns the matrix indices of each rank, in increasing order."""
+    import heapq
+
+    if world < 1:
+        raise ValueError("world >= 1")
+    order = sorted(range(len(ns)), key=lambda k: (-int(ns[k]), k))
+    heap = [(0, r) for r in range(world)]
+    shards: List[List[int]] = [[] for _ in range(world)]
+    for k in order:
+        load, r = heapq.heappop(heap)
+        shards[r].append(k)
+        heapq.heappush(heap, (load + (1 << (int(ns[k]) - 1)), r))
+    return [sorted(s) for s in shards]

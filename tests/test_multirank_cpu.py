@@ -79,3 +79,24 @@ def test_dd_add_exact_cancellation():
     b = (-1.0, 3e-20)
     s = M.dd_add(a, b)
     assert s[0] + s[1] == pytest.approx(4e-20, rel=1e-12)
+
+
+def test_shard_batch_balances_cost():
+    from paper_1904_06229_gb300 import workloads as W
+
+    ns = W.batch_sizes(5000, 3)
+    for world in (1, 2, 3, 8):
+        shards = M.shard_batch(ns, world)
+        flat = sorted(k for s in shards for k in s)
+        assert flat == list(range(len(ns)))  # every matrix exactly once
+        loads = [sum(1 << (int(ns[k]) - 1) for k in s) for s in shards]
+        # greedy deal in decreasing cost: the spread is at most the largest item
+        assert max(loads) - min(loads) <= 1 << (int(max(ns)) - 1)
+        assert max(loads) <= sum(loads) / world + (1 << (int(max(ns)) - 1))
+
+
+def test_shard_batch_small_cases():
+    assert M.shard_batch([3, 3, 3, 3], 2) == [[0, 2], [1, 3]]
+    assert M.shard_batch([5], 3) == [[0], [], []]
+    with pytest.raises(ValueError):
+        M.shard_batch([4], 0)
