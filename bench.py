@@ -64,7 +64,7 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "configs.json")
 # kernel (profiles/k_walk_xp_pdf_c128_n40_haar.md); the issue-slot fraction
 # below divides it by the scheduler rate of 4 warp instructions per clock
 # per SM at the SM clock sampled during the run.
-ISSUED_LANE_INSTR_PER_CODE_N40 = 1368
+ISSUED_LANE_INSTR_PER_CODE_N40 = 1281
 
 
 def workload_matrix(n=N_ORDER, seed=SEED):

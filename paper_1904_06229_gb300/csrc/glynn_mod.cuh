@@ -304,8 +304,8 @@ template <int N>
 __global__ void __launch_bounds__(kModThreads) k_mod(const int8_t* __restrict__ A, ModConsts c, uint64_t count,
                                                      uint64_t* __restrict__ partials) {
   // Column stride: whole int4 loads, and an odd number of 16-byte units, so
-  // that the columns that different threads read at once (each thread is at
-  // its own Gray code) start in different shared-memory banks.
+  // that when the lanes of a warp do read different columns (the few steps
+  // where their Gray codes differ), those start in different banks.
   constexpr int NP = (((N + 3) & ~3) / 4) % 2 == 1 ? ((N + 3) & ~3) : ((N + 3) & ~3) + 4;
   __shared__ __align__(16) int sA2[N * NP];   // +2 a_ij, column-major
   __shared__ __align__(16) int sA2m[N * NP];  // -2 a_ij
@@ -336,16 +336,25 @@ __global__ void __launch_bounds__(kModThreads) k_mod(const int8_t* __restrict__ 
   __syncthreads();
   // |v_i| <= b_i = sum_j |a_ij| <= b = max_i b_i
   const uint64_t b = (uint64_t)sMax;
+  // Per-thread ranges of equal length L, rounded up to a multiple of an
+  // alignment a (256, or the power of two at or above the length when that is
+  // smaller), so all threads start at codes congruent modulo a: the lanes of
+  // a warp then flip the same column with the same sign on all but a few
+  // steps in a, and the column read is a shared-memory broadcast.
   const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint64_t q0 = count / T, rem = count % T;
-  const uint64_t r = gid * q0 + (gid < rem ? gid : rem);
-  const uint64_t end = r + q0 + (gid < rem ? 1 : 0);
+  uint64_t L = (count + T - 1) / T;
+  uint64_t align = 256;
+  while (align > 1 && (align >> 1) >= L) align >>= 1;
+  L = (L + align - 1) & ~(align - 1);
+  const uint64_t s0 = gid * L;
+  const uint64_t r = s0 < count ? s0 : count;
+  const uint64_t end = s0 + L < count ? s0 + L : count;
 
-  // Exact sums: every partial sum of a thread is below (q0 + 1) prod_i b_i;
+  // Exact sums: every partial sum of a thread is below (L + 1) prod_i b_i;
   // bits = log2 of that bound, plus the sign and a margin for rounding of the
   // logarithms (fixed summation order, the same in every thread).
-  double lg = log2((double)(q0 + 1));
+  double lg = log2((double)(L + 1));
   for (int i = 0; i < N; ++i) lg += sLog[i];
   const int bits = (int)ceil(lg) + 2;
   const int hsix = pow_bound(b, 6) < (1ull << 31);  // factors of 6 rows fit in int32

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 import torch
 
+import _tolerance as T
 from oracle import oracle as O
 from paper_1904_06229_gb300 import longrun as L
 from paper_1904_06229_gb300 import perm as P
@@ -18,13 +19,18 @@ pytestmark = pytest.mark.gpu
 
 
 def test_checkpointed_run_matches_single_call(tmp_path):
+    """An interrupted and resumed run in 2^21-code chunks against the oracle
+    (the 1e-10 bar) and against one uninterrupted call (the two split the sum
+    differently, so they agree to rounding: 1e-11)."""
     A = W.haar_submatrix(26, 676, 12)
     path = str(tmp_path / "st.json")
     assert L.run(A, path, chunk_codes=1 << 21, max_chunks=5) is None
     got = L.run(A, path, chunk_codes=1 << 21)
     one = P.perm_c128(torch.from_numpy(A).cuda()).cpu().numpy()
-    ref = complex(one[0], one[1])
-    assert abs(got - ref) <= 1e-12 * abs(ref)
+    single = complex(one[0], one[1])
+    re, im, asum = O.per(A)
+    T.check(got, complex(float(re), float(im)), float(asum), 26, T.U_DF, "checkpointed n=26")
+    assert abs(got - single) <= 1e-11 * abs(single)
 
 
 def test_status_wait_limit(monkeypatch):
