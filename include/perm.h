@@ -203,8 +203,9 @@ int perm_sparse_partition(const double* A_host, int n, int* block, uint64_t* cou
  * The matrices are grouped by order, largest first, and each order's
  * (matrix, code chunk) work items go to one of three persistent kernels: one
  * warp per item with exact fixed-point rows, or one block of 128 threads per
- * item with the default packed double-float walk (a variant allowing two or
- * three blocks per SM); each kernel takes its items from an atomic ticket,
+ * item with the default packed double-float walk (128 threads allowing two
+ * or three blocks per SM, or 256 threads); each kernel takes its items from
+ * an atomic ticket,
  * and a last kernel adds each matrix's item partials in a fixed order.  The
  * kernel and the codes per thread of each order come from a per-GPU tuning
  * table (perm_batch_autotune, perm_batch_tuning); untuned orders take
@@ -244,8 +245,9 @@ int perm_batch_plans(int* built);
 int perm_batch_stats(const double* const* ptrs, const int* ns, int count, double* out, double* stats, void* stream);
 
 /* Fill the batch tuning table for orders n_lo..n_hi on the current device by
- * timing, per order, each kernel (warp per item, block per item with up to
- * 255 or 168 registers) at each chunk length 16 .. 8192 codes per thread on
+ * timing, per order, each kernel (warp per item; block of 128 threads per
+ * item with up to 255 or 168 registers; block of 256 threads per item) at
+ * each chunk length 16 .. 8192 codes per thread on
  * synthetic input (blocking, a few seconds).  Returns PERM_OK or an error. */
 int perm_batch_autotune(int n_lo, int n_hi);
 
@@ -253,13 +255,14 @@ int perm_batch_autotune(int n_lo, int n_hi);
 #define PERM_BATCH_WARP 1  /* one warp per item, exact fixed-point rows */
 #define PERM_BATCH_CTA 2   /* one block of 128 threads per item, packed double-float walk, 2 blocks per SM */
 #define PERM_BATCH_CTA3 3  /* the same with 3 blocks per SM (168 registers) */
+#define PERM_BATCH_CTA256 4 /* one block of 256 threads per item, 1 block per SM */
 
 /* Read (set = 0) or replace (set != 0) the batch tuning table of `device`
  * for the row arithmetic PERM_ROWS selects: L and kind are HOST arrays of 33
  * ints; for order n, kind[n] is the kernel (PERM_BATCH_*) and L[n] the codes
  * per thread (per lane for the warp kernel), both 0 when not tuned (index 0
  * unused).  On set every entry must be 0 in both arrays or a power of two in
- * 16 .. 2^24 with a kind 1..3 (PERM_EINVAL otherwise, nothing changed).
+ * 16 .. 2^24 with a kind 1..4 (PERM_EINVAL otherwise, nothing changed).
  * Host only: no CUDA call is made, so a table saved from one process can be
  * loaded into another before its first batch (the choices change only speed,
  * never results beyond rounding order). */

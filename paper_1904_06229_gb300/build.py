@@ -49,6 +49,7 @@ SOURCES = [
     "batch.cu",
     "batch_cta2.cu",
     "batch_cta3.cu",
+    "batch_cta256.cu",
     "perm_abi.cu",
     "peak.cu",
     "noalloc.cu",

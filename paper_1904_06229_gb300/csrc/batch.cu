@@ -10,11 +10,11 @@
 // table (batch_common.cuh), so a plan is O(count) to build and holds one int
 // per matrix plus four doubles per item.
 //
-// Kernels.  Orders go to one of three persistent kernels, chosen per order by
+// Kernels.  Orders go to one of four persistent kernels, chosen per order by
 // the tuner: one warp per item with exact fixed-point rows (k_batch here; its
-// lanes share an item, so small orders need little staging), or one block of
-// 128 threads per item with the packed double-float walk (batch_cta.cuh,
-// allowing 2 or 3 blocks per SM).  Each kernel pulls tickets from its own
+// lanes share an item, so small orders need little staging), or one block per
+// item with the packed double-float walk (batch_cta.cuh: 128 threads allowing
+// 2 or 3 blocks per SM, or 256 threads).  Each kernel pulls tickets from its own
 // counter, largest orders first.  A finalize kernel adds each matrix's item
 // partials in item order (deterministic) and applies 2 (-1)^(n-1).
 //
@@ -291,7 +291,8 @@ int batch_resident_blocks_rows(RowMode rows) {
 }
 
 int batch_resident_blocks_cta(int kind) {
-  return kind == kBatchCta3 ? batch_resident_cta_minb3() : batch_resident_cta_minb2();
+  return kind == kBatchCta3 ? batch_resident_cta_minb3()
+                            : kind == kBatchCta256 ? batch_resident_cta256() : batch_resident_cta_minb2();
 }
 
 cudaError_t batch_launch_warp(const BatchArgs* ba, const int* perm, const BatchTable& tab, double* partials,
@@ -307,8 +308,9 @@ cudaError_t batch_launch_warp(const BatchArgs* ba, const int* perm, const BatchT
 
 cudaError_t batch_launch_cta(int kind, const BatchArgs* ba, const int* perm, const BatchTable& tab, double* partials,
                              unsigned long long* ticket, int* status, cudaStream_t s) {
-  return kind == kBatchCta3 ? batch_launch_cta_minb3(ba, perm, tab, kind, partials, ticket, status, s)
-                            : batch_launch_cta_minb2(ba, perm, tab, kind, partials, ticket, status, s);
+  if (kind == kBatchCta3) return batch_launch_cta_minb3(ba, perm, tab, kind, partials, ticket, status, s);
+  if (kind == kBatchCta256) return batch_launch_cta256(ba, perm, tab, kind, partials, ticket, status, s);
+  return batch_launch_cta_minb2(ba, perm, tab, kind, partials, ticket, status, s);
 }
 
 void preload_batch_kernels() {
@@ -320,6 +322,7 @@ void preload_batch_kernels() {
   batch_resident_blocks_rows(kRowsFixed);
   batch_resident_cta_minb2();
   batch_resident_cta_minb3();
+  batch_resident_cta256();
 }
 
 }  // namespace perm
@@ -397,7 +400,9 @@ Choice resolve_choice(int dev, RowMode rows) {
   return c;
 }
 
-uint64_t threads_per_item(int kind) { return kind == kBatchWarp ? 32ull : (uint64_t)kBatchCtaThreads; }
+uint64_t threads_per_item(int kind) {
+  return kind == kBatchWarp ? 32ull : kind == kBatchCta256 ? 256ull : (uint64_t)kBatchCtaThreads;
+}
 
 // Most work items one plan holds (2 GiB of partials).
 constexpr uint64_t kMaxItems = 1ull << 26;
@@ -479,7 +484,7 @@ int build_plan(Plan& p, const int* ns, int count, const Choice& ch, RowMode rows
   for (int k = 0; k < count; ++k) perm[fill[ns[k]]++] = k;
   BatchTable& t = p.tab;
   std::memset(&t, 0, sizeof(t));
-  uint64_t kb[kBatchKinds] = {0, 0, 0, 0}, gb = 0;
+  uint64_t kb[kBatchKinds] = {}, gb = 0;
   for (int n = kBatchNMax; n >= 1; --n) {
     if (!cnt[n]) continue;
     const int kind = ch.kind[n];
@@ -528,6 +533,8 @@ int build_plan(Plan& p, const int* ns, int count, const Choice& ch, RowMode rows
       el = batch_launch_cta(kBatchCta, ba, dperm, t, parts, tk + kBatchCta, status, cs);
     if (el == cudaSuccess && kb[kBatchCta3])
       el = batch_launch_cta(kBatchCta3, ba, dperm, t, parts, tk + kBatchCta3, status, cs);
+    if (el == cudaSuccess && kb[kBatchCta256])
+      el = batch_launch_cta(kBatchCta256, ba, dperm, t, parts, tk + kBatchCta256, status, cs);
     if (el == cudaSuccess) {
       k_batch_finalize<<<(count + 127) / 128, 128, 0, cs>>>(ba, dperm, t, parts, count);
       el = cudaGetLastError();
@@ -650,8 +657,8 @@ int autotune_order(int dev, int n) {
   double best_rate = 0.0;
   int best_kind = kBatchWarp, best_L = default_L_warp(n);
   if (!warp_only(rows)) default_choice(n, best_kind, best_L);
-  const int kinds[3] = {kBatchWarp, kBatchCta, kBatchCta3};
-  for (int ki = 0; ki < 3 && rc == PERM_OK; ++ki) {
+  const int kinds[4] = {kBatchWarp, kBatchCta, kBatchCta3, kBatchCta256};
+  for (int ki = 0; ki < 4 && rc == PERM_OK; ++ki) {
     const int kind = kinds[ki];
     if (kind != kBatchWarp && warp_only(rows)) continue;
     for (int L = 16; L <= 8192 && rc == PERM_OK; L <<= 1) {
@@ -680,7 +687,7 @@ int perm_batch_tuning(int device, int* L, int* kind, int set) {
   if (!L || !kind) return PERM_ENULL;
   if (device < 0 || device >= 64) return PERM_EINVAL;
   if (set) {
-    // every entry 0 (untuned) or a power of two in 16 .. 2^24 codes, with a kind 1..3
+    // every entry 0 (untuned) or a power of two in 16 .. 2^24 codes, with a kind 1..4
     for (int n = 1; n <= kBatchNMax; ++n) {
       const int v = L[n], k = kind[n];
       if ((v == 0) != (k == 0)) return PERM_EINVAL;

@@ -9,9 +9,10 @@
 // the chunk over its threads in congruent ranges, walks, and writes the
 // item's double-double partial.  The order is a runtime value; each order
 // has its own instantiation of the walk (register arrays need a compile-time
-// order), selected per item.  MINB sets the blocks per SM the register
-// allocation must allow (2: up to 255 registers; 3: up to 168), one of the
-// tuner's choices per order.
+// order), selected per item.  THREADS is the block size (128 or 256: the
+// threads that share one item) and MINB the blocks per SM the register
+// allocation must allow (2 blocks of 128: up to 255 registers; 3: up to 168;
+// 1 block of 256: up to 255), the tuner's choices per order.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -23,7 +24,6 @@
 
 namespace perm {
 
-constexpr int kCtaThreads = kBatchCtaThreads;
 constexpr size_t kCtaSmem = XpShape<kBatchNMax, false>::smem_bytes;  // tables of the largest order
 
 template <int N>
@@ -67,14 +67,14 @@ __device__ __forceinline__ void cta_case(const double* __restrict__ A, const Bat
   }
 }
 
-template <int MINB>
-__global__ void __launch_bounds__(kCtaThreads, MINB)
+template <int MINB, int THREADS>
+__global__ void __launch_bounds__(THREADS, MINB)
     k_batch_cta(const BatchArgs* __restrict__ ba, const int* __restrict__ perm, const __grid_constant__ BatchTable tab,
                 int kind, double* __restrict__ partials, unsigned long long* __restrict__ ticket,
                 int* __restrict__ status, int tile_log) {
   extern __shared__ __align__(16) float4 csm[];
   __shared__ int sG[kBatchNMax];
-  __shared__ dd sRed[8];
+  __shared__ dd sRed[2 * (THREADS / 32)];
   __shared__ unsigned long long sTicket;
   const double* const* ptrs = ba->ptrs;
   for (;;) {
@@ -88,18 +88,18 @@ __global__ void __launch_bounds__(kCtaThreads, MINB)
   }
 }
 
-template <int MINB>
+template <int MINB, int THREADS>
 struct CtaKernel {
   static int resident() {
     static std::atomic<int> cached[64];  // per device
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
     if (cached[dev]) return cached[dev];
-    if (cudaFuncSetAttribute(k_batch_cta<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCtaSmem) !=
+    if (cudaFuncSetAttribute(k_batch_cta<MINB, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCtaSmem) !=
         cudaSuccess)
       return 0;
     int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_cta<MINB>, kCtaThreads, kCtaSmem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_cta<MINB, THREADS>, THREADS, kCtaSmem) !=
         cudaSuccess)
       return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
@@ -111,7 +111,7 @@ struct CtaKernel {
                             unsigned long long* ticket, int* status, cudaStream_t s) {
     const int grid = resident();
     if (grid < 1) return cudaErrorInvalidConfiguration;
-    k_batch_cta<MINB><<<grid, kCtaThreads, kCtaSmem, s>>>(ba, perm, tab, kind, partials, ticket, status,
+    k_batch_cta<MINB, THREADS><<<grid, THREADS, kCtaSmem, s>>>(ba, perm, tab, kind, partials, ticket, status,
                                                          pdf_tile_log());
     return cudaGetLastError();
   }

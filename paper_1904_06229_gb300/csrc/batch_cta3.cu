@@ -5,9 +5,9 @@ namespace perm {
 
 cudaError_t batch_launch_cta_minb3(const BatchArgs* ba, const int* perm, const BatchTable& tab, int kind,
                                    double* partials, unsigned long long* ticket, int* status, cudaStream_t s) {
-  return CtaKernel<3>::launch(ba, perm, tab, kind, partials, ticket, status, s);
+  return CtaKernel<3, kBatchCtaThreads>::launch(ba, perm, tab, kind, partials, ticket, status, s);
 }
 
-int batch_resident_cta_minb3() { return CtaKernel<3>::resident(); }
+int batch_resident_cta_minb3() { return CtaKernel<3, kBatchCtaThreads>::resident(); }
 
 }  // namespace perm

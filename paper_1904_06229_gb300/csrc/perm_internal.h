@@ -131,8 +131,9 @@ enum BatchKind : int {
   kBatchWarp = 1,  // one warp per item, exact fixed-point rows (batch.cu: k_batch)
   kBatchCta = 2,   // one block of 128 threads per item, packed double-float walk, 255 registers (batch_cta.cu)
   kBatchCta3 = 3,  // the same with a 168-register cap (three blocks per SM)
+  kBatchCta256 = 4,  // one block of 256 threads per item, one block per SM
 };
-constexpr int kBatchKinds = 4;
+constexpr int kBatchKinds = 5;
 constexpr int kBatchCtaThreads = 128;  // threads of a block-per-item kernel
 
 // Where the pointers of one call live: set by a one-thread kernel before each
@@ -171,6 +172,9 @@ cudaError_t batch_launch_cta_minb3(const BatchArgs* ba, const int* perm, const B
                                    double* partials, unsigned long long* ticket, int* status, cudaStream_t s);
 int batch_resident_cta_minb2();
 int batch_resident_cta_minb3();
+cudaError_t batch_launch_cta256(const BatchArgs* ba, const int* perm, const BatchTable& tab, int kind,
+                                double* partials, unsigned long long* ticket, int* status, cudaStream_t s);
+int batch_resident_cta256();
 
 // Per-device status word (device int, OR-ed by kernels; read and cleared by
 // perm_last_status).  Allocated on first use.

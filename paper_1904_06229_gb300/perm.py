@@ -363,14 +363,15 @@ def perm_batch_autotune(n_lo: int, n_hi: int) -> None:
     _check(load().perm_batch_autotune(int(n_lo), int(n_hi)), "perm_batch_autotune")
 
 
-BATCH_KINDS = {"warp": 1, "cta": 2, "cta3": 3}
+BATCH_KINDS = {"warp": 1, "cta": 2, "cta3": 3, "cta256": 4}
 
 
 def perm_batch_tuning(device: int, L: Optional[Sequence[int]] = None, kind: Optional[Sequence[int]] = None):
     """Read the batch tuning table of `device` (L and kind None), or replace it
     (33 ints each: for order n, L[n] codes per thread and kind[n] the kernel,
-    1 warp per item, 2 block per item, 3 block per item with three blocks per
-    SM; 0 = untuned); returns the table in force afterwards as (L, kind)."""
+    1 warp per item, 2 block of 128 threads per item, 3 the same with three
+    blocks per SM, 4 block of 256 threads per item; 0 = untuned); returns the
+    table in force afterwards as (L, kind)."""
     buf = (ctypes.c_int * 33)()
     kbuf = (ctypes.c_int * 33)()
     if L is not None or kind is not None:

@@ -1,6 +1,6 @@
 """Batched permanents: each result against the oracle (the 1e-10 bar of
 tests/_tolerance.py) and against single launches of the same arithmetic;
-each of the three batch kernels forced through the tuning table; a call on a
+each of the four batch kernels forced through the tuning table; a call on a
 non-current stream; plan reuse with new pointers; the tuner; the statistics
 invariants of Sec. 3 as a loose systematic check."""
 import math
@@ -62,7 +62,7 @@ def tuning():
 
 
 def test_batch_vs_oracle_and_single():
-    """Default choices (warp kernel below order 16, block kernel above): every
+    """Default choices (warp kernel up to order 12, block kernels above): every
     result against the oracle, and against a single default launch."""
     ns, mats = W.batch_study(300, seed=11, n_lo=1, n_hi=20)
     out, dm = _batch(mats)
@@ -74,11 +74,12 @@ def test_batch_vs_oracle_and_single():
         assert abs(complex(*out[k]) - one) <= 1e-11 * abs(one) + 1e-300, (k, ns[k])
 
 
-@pytest.mark.parametrize("kind", [1, 2, 3])
+@pytest.mark.parametrize("kind", [1, 2, 3, 4])
 def test_each_kernel_kind(kind, tuning):
-    """All orders forced onto one kernel (1 warp per item, 2 block per item,
-    3 block per item at three blocks per SM), with chunks short enough that
-    the larger matrices span several items."""
+    """All orders forced onto one kernel (1 warp per item, 2 block of 128
+    threads per item, 3 the same at three blocks per SM, 4 block of 256
+    threads per item), with chunks short enough that the larger matrices span
+    several items."""
     tuning(kind, L_warp=16, L_cta=16)
     ns, mats = W.batch_study(120, seed=21 + kind, n_lo=1, n_hi=22)
     out, _ = _batch(mats)
@@ -153,7 +154,7 @@ def test_autotune_fills_table(tuning):
     L, K = P.perm_batch_tuning(dev)
     print("tuned kinds", K[10:18], "lengths", L[10:18])
     for n in range(10, 18):
-        assert K[n] in (1, 2, 3) and L[n] >= 16 and (L[n] & (L[n] - 1)) == 0
+        assert K[n] in (1, 2, 3, 4) and L[n] >= 16 and (L[n] & (L[n] - 1)) == 0
     ns, mats = W.batch_study(60, seed=15, n_lo=10, n_hi=17)
     out, _ = _batch(mats)
     _check_vs_oracle(out, ns, mats, every=3, n_max=17, what="tuned")

@@ -21,7 +21,7 @@ def test_get_set_round_trip():
     L, K = [0] * 33, [0] * 33
     for n in range(4, 33):
         L[n] = 1 << (4 + n % 8)
-        K[n] = 1 + n % 3
+        K[n] = 1 + n % 4
     assert P.perm_batch_tuning(dev, L, K) == (L, K)
     assert P.perm_batch_tuning(dev) == (L, K)
     assert P.perm_batch_tuning(dev + 1) == ([0] * 33, [0] * 33)  # per device
@@ -45,7 +45,7 @@ def test_set_rejects_bad_lengths(bad):
     P.perm_batch_tuning(dev, [0] * 33, [0] * 33)
 
 
-@pytest.mark.parametrize("kind,L", [(4, 64), (-1, 64), (0, 64), (2, 0)])
+@pytest.mark.parametrize("kind,L", [(5, 64), (-1, 64), (0, 64), (2, 0)])
 def test_set_rejects_bad_kinds(kind, L):
     dev = 10
     Ls, Ks = [0] * 33, [0] * 33
