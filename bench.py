@@ -64,7 +64,7 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "configs.json")
 # kernel (profiles/k_walk_xp_pdf_c128_n40_haar.md); the issue-slot fraction
 # below divides it by the scheduler rate of 4 warp instructions per clock
 # per SM at the SM clock sampled during the run.
-ISSUED_LANE_INSTR_PER_CODE_N40 = 1281
+ISSUED_LANE_INSTR_PER_CODE_N40 = 1252
 
 
 def workload_matrix(n=N_ORDER, seed=SEED):
@@ -237,18 +237,19 @@ def pdf_fp32_ops(n):
     rows and products, glynn_walk_xp.cuh), counted from its arithmetic: per
     row pair and Gray step an 11-operation double-float add on each of the two
     components (two rows per packed operation); per term NP - 1 packed complex
-    double-float products of 32 packed operations, 4-operation packed
-    renormalisations (every 8 factors of a chain, and at its end), and one
-    scalar complex double-float product of 32 operations joining the lanes."""
+    double-float products of 32 packed operations (the chains' steps and the
+    joins of three chain pairs), 4-operation packed renormalisations (every 8
+    factors of a chain and at its end), and one scalar complex double-float
+    product of 32 operations joining the two lanes."""
     NP = (n + 1) // 2
-    CP = 2 if NP >= 2 else 1
+    CP = min(3, NP)
     lens, ren = [1] * CP, CP
     for k in range(CP, NP):
         q = k % CP
         lens[q] += 1
         if lens[q] % 8 == 0 and k + CP < NP:
             ren += 1
-    muls = (NP - CP) + (1 if CP == 2 else 0)
+    muls = NP - 1
     return NP * 2 * 11 * 2 + muls * 32 * 2 + ren * 4 * 2 + 32
 
 

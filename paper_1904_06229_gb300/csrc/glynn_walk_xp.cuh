@@ -5,14 +5,14 @@
 // (the .x and .y lanes of a float2), so each packed FP32 instruction of
 // sm_100+ (add/sub/mul/fma .f32x2) works on two rows.  On GB300 a packed FMA
 // issues at half the scalar rate but does two FMAs, so the FP32 pipe does the
-// same work with half the instructions.  The product Prod_i v_i runs as four
-// double-float chains held in two packed chain pairs: chain pair c multiplies
-// the row pairs c, c+2, c+4, ... (each step a complex double-float product:
-// exact FP32 products by FMA, TwoSum for the sums, about 48 significant
-// bits); the chains are renormalised by powers of two every eight factors and
-// at the end, multiplied together, and the term is rebuilt as FP64 (high and
-// low parts converted and scaled by 2^E with the sign folded in) and summed
-// into FP64 run sums folded into double-double.
+// same work with half the instructions.  The product Prod_i v_i runs as six
+// double-float chains held in three packed chain pairs: chain pair c
+// multiplies the row pairs c, c+3, c+6, ... (each step a complex double-float
+// product: exact FP32 products by FMA, TwoSum for the sums, about 48
+// significant bits); the chains are renormalised by powers of two every eight
+// factors and at the end, multiplied together, and the term is rebuilt as
+// FP64 (high and low parts converted and scaled by 2^E with the sign folded
+// in) and summed into FP64 run sums folded into double-double.
 //
 // Row scale.  Row i of A is scaled by 2^G_i so that max(sum_j |Re a_ij|,
 // sum_j |Im a_ij|) 2^G_i < 1; every row sum in Glynn's form v_i = sum_j e_j
@@ -22,10 +22,10 @@
 // unevaluated pair of floats renormalised after every step (TwoSum, then
 // FastTwoSum: about 48 significant bits relative to the row sum itself), the
 // columns are the double-float roundings of the exact integer columns, and
-// every 128 codes each row is re-seeded from its exact int64 value (entries
-// rounded once to 2^-61 of the row scale, as fine as the fixed-point walk),
-// so the rounding errors of the steps stay independent and average out over
-// the sum.
+// every 1024 codes (pdf_tile_log()) each row is re-seeded from its exact
+// int64 value (entries rounded once to 2^-61 of the row scale, as fine as the
+// fixed-point walk), so the rounding errors of the steps stay independent and
+// average out over the sum.
 //
 // Exact float-pair rows (kRowsPair).  Each scaled entry is rounded once to
 // the grid 2^-47 (a 48-bit fixed point relative to the row's largest possible
@@ -42,6 +42,12 @@
 // Warp-uniform steps.  Thread ranges are congruent modulo 2^8 codes, so the
 // lanes of a warp flip the same column with the same sign on all but one step
 // in 128: the column read is a shared-memory broadcast.
+//
+// The number of packed chain pairs (3) was measured against 2 and 4 at
+// n = 40 and 48: 3 is 3 % faster than 2 at n = 40 and equal at 48; 4 spills
+// at n = 48.  Renormalising the rows every second step instead of every step
+// (saving 3 of the 11 packed operations of half the updates) measured 3 %
+// slower, with the step loop unrolled by two.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -62,6 +68,11 @@ constexpr int kPdfGrid = 61;      // double-float rows: exact int64 seeds in uni
 // double-float rows: re-seeded every 2^tile_log codes (a kernel argument: pdf_tile_log())
 constexpr int kXpAlignLog = 8;    // thread ranges are congruent modulo 2^8 codes
 constexpr int kXpRenormEvery = 8; // chain renormalisation period (factors)
+#ifndef PERM_XP_CHAIN_PAIRS
+#define PERM_XP_CHAIN_PAIRS 3
+#endif
+
+constexpr int kXpChainPairs = PERM_XP_CHAIN_PAIRS;  // packed chain pairs of the product
 
 template <int N>
 constexpr int kPairs = (N + 1) / 2;  // row pairs (an odd order gets a constant row 1)
@@ -199,7 +210,7 @@ __device__ __forceinline__ double signed_pow2(int E, uint32_t negative) {
 template <int N>
 __device__ __forceinline__ void xp_product(const P4 (&v)[kPairs<N>], cdf& z, int& E) {
   constexpr int NP = kPairs<N>;
-  constexpr int CP = NP >= 2 ? 2 : 1;  // packed chain pairs
+  constexpr int CP = NP >= kXpChainPairs ? kXpChainPairs : NP;  // packed chain pairs
   P4 c[CP];
   int ex[CP], ey[CP];
   int len[CP];
@@ -213,10 +224,11 @@ __device__ __forceinline__ void xp_product(const P4 (&v)[kPairs<N>], cdf& z, int
   }
 #pragma unroll
   for (int q = 0; q < CP; ++q) p4_renorm(c[q], ex[q], ey[q]);
-  if constexpr (CP == 2) {
-    c[0] = p4_mul(c[0], c[1]);
-    ex[0] += ex[1];
-    ey[0] += ey[1];
+#pragma unroll
+  for (int q = 1; q < CP; ++q) {
+    c[0] = p4_mul(c[0], c[q]);
+    ex[0] += ex[q];
+    ey[0] += ey[q];
   }
   const cdf x{c[0].hr.x, c[0].lr.x, c[0].hi.x, c[0].li.x};
   const cdf y{c[0].hr.y, c[0].lr.y, c[0].hi.y, c[0].li.y};
