@@ -72,19 +72,21 @@ typedef enum {
  * rounded once to 2^-61 of the row scale), so the step errors stay
  * independent.  The product of the n row sums is formed in double-float
  * (exact FP32 products by fused multiply-add, TwoSum sums) in four chains
- * renormalised by powers of two; each term is rebuilt as FP64.  Real A:
- * exact 64-bit fixed-point row sums (entries rounded once to 2^-61 of the
- * row's largest sum) and FP64 products from doubles built by integer bit
- * operations.  Each thread's terms are summed in FP64 over runs of at most
+ * renormalised by powers of two; each term is rebuilt as FP64.  Real A: the
+ * same arithmetic with one component per row.  Each thread's terms are
+ * summed in FP64 over runs of at most
  * 4096 codes and folded into a double-double accumulator; the per-thread
  * accumulators are combined with warp shuffles and a fixed-order tree in
  * double-double.  out: the permanent, double-double rounded to double(s).
  * Observed error against the long-double oracle: about 1e-13 relative on
- * n = 40 and 48 Haar slices (within 1e-10 for every tested configuration).
- * The environment variable PERM_ROWS selects another row arithmetic for the
- * complex entry points: "fixed" (exact 64-bit fixed-point row sums; about
- * 0.85 n of the factors multiplied in 64-bit integer block floating point,
- * the rest in FP64: about 1e-15, 2.4x slower at n = 40), "fp64" (FP64 row
+ * n = 40 and 48 Haar slices (within 1e-10 for every tested configuration);
+ * the error grows with the sum's condition number sum|t| / |per|, which is
+ * large for real Gaussian matrices (1e-10 from the exact walk at n = 36).
+ * The environment variable PERM_ROWS selects another row arithmetic:
+ * "fixed" (exact 64-bit fixed-point row sums; complex: about 0.85 n of the
+ * factors multiplied in 64-bit integer block floating point, the rest in
+ * FP64; real: FP64 products; about 1e-15 per term, 2.7x (complex) and 3.5x
+ * (real) slower), "fp64" (FP64 row
  * sums restarted from their definition every 4096 codes), "df" (unpacked
  * double-float rows and products) or "pair" (exact float-pair row sums on a
  * 48-bit fixed grid: 1.4x faster than the default at n = 40, but the grid's

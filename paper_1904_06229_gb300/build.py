@@ -39,6 +39,8 @@ SOURCES = [
     "walk_xp_c128_hi.cu",
     "walk_pdf_c128_lo.cu",
     "walk_pdf_c128_hi.cu",
+    "walk_pdf_r64_lo.cu",
+    "walk_pdf_r64_hi.cu",
     "glynn_mod.cu",
     "mod_lo.cu",
     "mod_mid.cu",

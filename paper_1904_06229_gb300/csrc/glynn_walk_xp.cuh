@@ -236,19 +236,19 @@ __device__ __forceinline__ void xp_product(const P4 (&v)[kPairs<N>], cdf& z, int
   E = ex[0] + ey[0];
 }
 
-// Row scales 2^G_i (sG) of the staging step.  Returns (block-uniform)
-// whether any entry is non-finite.
-template <int N>
+// Row scales 2^G_i (sG) of the staging step (E = 2: complex entries, 1:
+// real).  Returns (block-uniform) whether any entry is non-finite.
+template <int N, int E = 2>
 __device__ __forceinline__ bool xp_row_scales(const double* __restrict__ A, int* sG, int* status) {
   int bad = 0;
   if (threadIdx.x < N) {
     const int i = threadIdx.x;
     double mx = 0.0;
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
+    for (int c = 0; c < E; ++c) {
       double s = 0.0;
       for (int j = 0; j < N; ++j) {
-        const double v = A[((size_t)i * N + j) * 2 + c];
+        const double v = A[((size_t)i * N + j) * E + c];
         bad |= not_finite(v) ? 1 : 0;
         s += fabs(v);
       }

@@ -168,7 +168,7 @@ RowMode rows_from_env() {
   if (e && std::strcmp(e, "df") == 0) return kRowsDf;
   if (e && std::strcmp(e, "pair") == 0) return kRowsPair;
   if (e && std::strcmp(e, "fixed") == 0) return kRowsFixed;
-  return kRowsPdf;  // complex FP64-product walks; the others take kRowsFixed
+  return kRowsPdf;  // FP64-product walks; the FP32-product ones take kRowsFixed
 }
 
 int pdf_tile_log() {
@@ -186,6 +186,8 @@ int walk_resident_blocks(int n, bool cplx, ProductMode mode, RowMode rows) {
     return n <= 32 ? walk_blocks_xp_c128_lo(n) : walk_blocks_xp_c128_hi(n);
   if (rows == kRowsPdf && cplx && mode == kProdF64)
     return n <= 32 ? walk_blocks_pdf_c128_lo(n) : walk_blocks_pdf_c128_hi(n);
+  if (rows == kRowsPdf && !cplx && mode == kProdF64)
+    return n <= 32 ? walk_blocks_pdf_r64_lo(n) : walk_blocks_pdf_r64_hi(n);
   if (rows == kRowsDf || rows == kRowsPair || rows == kRowsPdf) rows = kRowsFixed;
   if (rows == kRowsFixed) {
     if (mode == kProdF64) {
@@ -207,6 +209,8 @@ cudaError_t walk_launch(bool cplx, ProductMode mode, const WalkArgs& a, RowMode 
     return a.n <= 32 ? walk_launch_xp_c128_lo(a) : walk_launch_xp_c128_hi(a);
   if (rows == kRowsPdf && cplx && mode == kProdF64)
     return a.n <= 32 ? walk_launch_pdf_c128_lo(a) : walk_launch_pdf_c128_hi(a);
+  if (rows == kRowsPdf && !cplx && mode == kProdF64)
+    return a.n <= 32 ? walk_launch_pdf_r64_lo(a) : walk_launch_pdf_r64_hi(a);
   if (rows == kRowsDf || rows == kRowsPair || rows == kRowsPdf) rows = kRowsFixed;
   if (rows == kRowsFixed) {
     if (mode == kProdF64) {

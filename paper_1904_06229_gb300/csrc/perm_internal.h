@@ -28,14 +28,14 @@ enum RowMode : int {
   kRowsPair = 3,   // exact float-pair row sums, packed double-float products (glynn_walk_xp.cuh);
                    // complex FP64-product walks only, the others use kRowsFixed
   kRowsPdf = 4,    // packed double-float row sums re-seeded from exact int64 and packed double-float
-                   // products (glynn_walk_xp.cuh); complex FP64-product walks only
+                   // products (glynn_walk_xp.cuh, glynn_walk_xr.cuh); FP64-product walks
 };
 constexpr int kRowModes = 5;
 
 // Row arithmetic for the floating-point entry points: PERM_ROWS=fp64 selects
 // kRowsF64, PERM_ROWS=df kRowsDf, PERM_ROWS=pair kRowsPair, PERM_ROWS=fixed
 // kRowsFixed, anything else (default) kRowsPdf, which the walks without a
-// packed variant (real, FP32-product, batch) take as kRowsFixed.
+// packed variant (FP32-product, warp batch kernel) take as kRowsFixed.
 RowMode rows_from_env();
 
 // Re-seed period (log2 codes) of the packed double-float walk: PERM_PDF_TILE_LOG
@@ -73,6 +73,10 @@ cudaError_t walk_launch_xp_c128_lo(const WalkArgs& a);  // exact float-pair rows
 cudaError_t walk_launch_xp_c128_hi(const WalkArgs& a);  // n in 33..64
 int walk_blocks_xp_c128_lo(int n);
 int walk_blocks_xp_c128_hi(int n);
+cudaError_t walk_launch_pdf_r64_lo(const WalkArgs& a);   // the same for real matrices, n in 1..32
+cudaError_t walk_launch_pdf_r64_hi(const WalkArgs& a);   // n in 33..64
+int walk_blocks_pdf_r64_lo(int n);
+int walk_blocks_pdf_r64_hi(int n);
 cudaError_t walk_launch_pdf_c128_lo(const WalkArgs& a);  // packed double-float rows and products, n in 1..32
 cudaError_t walk_launch_pdf_c128_hi(const WalkArgs& a);  // n in 33..64
 int walk_blocks_pdf_c128_lo(int n);
