@@ -573,6 +573,21 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk_fx(const double* __restri
 
   const bool bad = fx_stage<N, CPLX>(A, sP, sM, sV0, sEb, sF, status);
 
+  // FP64 products multiply the unscaled row values v_i 2^-63 (below 1/2 in
+  // magnitude, so no chain leaves the double range however the rows are
+  // scaled); the rows' scales 2^(eb_i - 1023) are applied once, to the
+  // thread's sum.  The FP32-product mode carries its exponents in integers.
+  const int* sE = sEb;
+  int scale = 0;
+  if constexpr (MODE == kProdF64) {
+    if (!bad) {
+      for (int i = 0; i < N; ++i) scale += sEb[i] - 1023;
+      if (threadIdx.x < N) sF[threadIdx.x] = 1023;  // sF is free after staging
+      __syncthreads();
+      sE = sF;
+    }
+  }
+
   uint64_t r, end;
   thread_range(first, count, r, end);
   dd accr{0.0, 0.0}, acci{0.0, 0.0};
@@ -580,9 +595,13 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk_fx(const double* __restri
     if constexpr (CPLX)
       thread_walk_c128_fx<N, MODE, true, S>(reinterpret_cast<const longlong2*>(sP),
                                             reinterpret_cast<const longlong2*>(sM),
-                                            reinterpret_cast<const longlong2*>(sV0), sEb, r, end, accr, acci);
+                                            reinterpret_cast<const longlong2*>(sV0), sE, r, end, accr, acci);
     else
-      thread_walk_r64_fx<N, MODE, S>(sP, sM, sV0, sEb, r, end, accr);
+      thread_walk_r64_fx<N, MODE, S>(sP, sM, sV0, sE, r, end, accr);
+    if constexpr (MODE == kProdF64) {
+      accr = dd{scalbn(accr.hi, scale), scalbn(accr.lo, scale)};
+      acci = dd{scalbn(acci.hi, scale), scalbn(acci.lo, scale)};
+    }
   } else {
     accr = dd{__longlong_as_double(0x7ff8000000000000ll), 0.0};
     acci = accr;

@@ -66,3 +66,52 @@ def test_complex_unit_entries(n, rows):
     u = T.unit(rows)
     T.check(gpu_c128(A), ref, float(asum), n, u, f"unit entries n={n}")
     T.check(gpu_c128(A.T), ref, float(asum), n, u, f"unit entries n={n}, transpose")
+
+
+@pytest.mark.parametrize("n", [7, 20])
+def test_rows_of_extreme_magnitude(n, rows):
+    """Rows scaled by 1e+-300 (not powers of two) and by 2^+-1000: each row's
+    own scale absorbs its magnitude, so the result matches the long-double
+    oracle of the scaled matrix (its range reaches 1e+-4932) at the bar."""
+    A = W.complex_gaussian(n, 950 + n)
+    s = np.ones(n)
+    s[0], s[1] = 1e300, 1e-300
+    s[2], s[3] = 2.0 ** 1000, 2.0 ** -1000
+    B = A * s[:, None]
+    re, im, asum = O.per(B)
+    ref = complex(float(re), float(im))
+    T.check(gpu_c128(B), ref, float(asum), n, T.unit(rows), f"extreme rows n={n}")
+
+
+@pytest.mark.parametrize("n", [6, 19])
+def test_zero_row_and_column(n, rows):
+    """A zero row makes every term zero: per = 0 exactly.  A zero column makes
+    per = 0 by cancellation of term pairs (codes that differ in that column),
+    which the walk reaches to within the rounding of those terms: the
+    a-posteriori bound with the oracle's sum of term magnitudes."""
+    A = W.complex_gaussian(n, 960 + n)
+    Z = A.copy()
+    Z[n // 2, :] = 0
+    assert gpu_c128(Z) == 0
+    Z = A.copy()
+    Z[:, n // 3] = 0
+    _, _, asum = O.per(Z)
+    T.check(gpu_c128(Z), 0.0, float(asum), n, T.unit(rows), f"zero column n={n}")
+    R = W.real_gaussian(n, 961 + n)
+    R[n - 1, :] = 0
+    out = P.perm_f64(torch.from_numpy(R).cuda()).cpu().numpy()
+    assert P.perm_last_status() == 0
+    assert out[0] == 0
+
+
+@pytest.mark.parametrize("n", [9, 17])
+def test_unequal_entries_within_a_row(n, rows):
+    """Entries spanning twelve orders of magnitude inside each row: the row
+    scale follows the largest, the small entries keep their relative weight
+    through the exact int64 (or double-float) columns."""
+    A = W.complex_gaussian(n, 970 + n)
+    mag = 10.0 ** np.random.default_rng(n).uniform(-6, 6, size=(n, n))
+    B = A * mag
+    re, im, asum = O.per(B)
+    ref = complex(float(re), float(im))
+    T.check(gpu_c128(B), ref, float(asum), n, T.unit(rows), f"unequal entries n={n}")
