@@ -51,8 +51,9 @@ namespace perm {
 
 constexpr int kBatchThreads = 128;
 constexpr int kBatchWarps = kBatchThreads / 32;
-// Per-warp shared slot (16-byte units): the FP64-row walk keeps A (n^2) and
-// w0 (n); the fixed-point walk keeps +2A (n^2), v0 (n) and two int rows.
+// Per-warp shared slot (16-byte units): the FP64-row walk keeps the row-scaled
+// A (n^2), w0 (n) and the row scale exponents; the fixed-point walk keeps +2A
+// (n^2), v0 (n) and two int rows.
 constexpr size_t kBatchSlot = (size_t)kBatchNMax * kBatchNMax + kBatchNMax + (2 * kBatchNMax * 4 + 15) / 16;
 constexpr size_t kBatchSmem = kBatchSlot * kBatchWarps * 16;
 
@@ -93,23 +94,47 @@ __global__ void __launch_bounds__(kBatchThreads)
     const int n = item.n;
     const double2* __restrict__ A = reinterpret_cast<const double2*>(ptrs[item.matrix]);
     bool bad = false;
+    // The walks multiply row values below 1 in magnitude (rows scaled by
+    // powers of two); the product of the rows' scales is applied once, to the
+    // item's sum, so no product chain leaves the double range however the
+    // rows of A are scaled.
+    int scale = 0;
     if constexpr (ROWS == kRowsFixed) {
       longlong2* sP = reinterpret_cast<longlong2*>(slot);
       longlong2* sV0 = sP + n * n;
       int* sEb = reinterpret_cast<int*>(sV0 + n);
       bad = fx_stage_warp_c128(A, n, sP, sV0, sEb, sEb + n);
+      if (!bad) {
+        for (int i = 0; i < n; ++i) scale += sEb[i] - 1023;
+        __syncwarp();
+        if (lane < n) sEb[lane] = 1023;  // products of v_i 2^-63
+        __syncwarp();
+      }
     } else {
-      // stage column-major (the single-matrix kernel's layout) and w0
+      // stage row-scaled entries column-major (the single-matrix kernel's
+      // layout) and w0; row i is scaled by 2^G_i, its largest part near 1
       double2* sA = slot;
       double2* sW0 = slot + n * n;
+      int* sG = reinterpret_cast<int*>(sW0 + n);
       int b = 0;
+      if (lane < n) {
+        double mx = 0.0;
+        for (int j = 0; j < n; ++j) {
+          const double2 v = A[lane * n + j];
+          b |= (not_finite(v.x) || not_finite(v.y)) ? 1 : 0;
+          mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+        }
+        sG[lane] = (mx > 0.0 && !b) ? -ilogb(mx) : 0;
+      }
+      bad = __any_sync(0xffffffffu, b) != 0;
+      __syncwarp();
+      for (int i = 0; i < n; ++i) scale -= sG[i];
       for (int idx = lane; idx < n * n; idx += 32) {
         const int i = idx / n, j = idx - i * n;
         const double2 v = A[idx];
-        b |= (not_finite(v.x) || not_finite(v.y)) ? 1 : 0;
-        sA[j * n + i] = v;
+        const int G = sG[i];
+        sA[j * n + i] = make_double2(scalbn(v.x, G), scalbn(v.y, G));
       }
-      bad = __any_sync(0xffffffffu, b) != 0;
       __syncwarp();
       if (lane < n) {
         double sr = 0.0, si = 0.0;
@@ -135,6 +160,8 @@ __global__ void __launch_bounds__(kBatchThreads)
     accr = dd_warp_sum(accr);
     acci = dd_warp_sum(acci);
     if (lane == 0) {
+      accr = dd{scalbn(accr.hi, scale), scalbn(accr.lo, scale)};
+      acci = dd{scalbn(acci.hi, scale), scalbn(acci.lo, scale)};
       double* o = partials + item.partial * 4;
       o[0] = accr.hi;
       o[1] = accr.lo;

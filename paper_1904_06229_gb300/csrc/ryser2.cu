@@ -115,6 +115,16 @@ __global__ void __launch_bounds__(kWalkThreads) k_ryser2(const double* __restric
     }
   }
   __syncthreads();
+  // The products multiply the unscaled row values v_i 2^-63 (below 1 in
+  // magnitude, so no chain leaves the double range however the rows are
+  // scaled); the rows' scales are applied once, to the thread's sum.
+  int scale = 0;
+  if (!any_bad) {
+    for (int i = 0; i < N; ++i) scale += sEb[i] - 1023;
+    __syncthreads();  // every thread has read sEb before it is overwritten
+    if (threadIdx.x < N) sEb[threadIdx.x] = 1023;
+    __syncthreads();
+  }
 
   uint64_t r, end;
   thread_range(0, total, r, end);
@@ -226,6 +236,8 @@ __global__ void __launch_bounds__(kWalkThreads) k_ryser2(const double* __restric
       accr = dd_add_d(accr, sr);
       acci = dd_add_d(acci, si);
     }
+    accr = dd{scalbn(accr.hi, scale), scalbn(accr.lo, scale)};
+    acci = dd{scalbn(acci.hi, scale), scalbn(acci.lo, scale)};
   }
   __syncthreads();
   block_store<true>(accr, acci, sRed, partials, 0);

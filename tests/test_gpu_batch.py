@@ -100,6 +100,27 @@ def test_fixed_rows_match_single_fixed_launches(monkeypatch):
     _check_vs_oracle(out, ns, mats, every=9)
 
 
+@pytest.mark.parametrize("rows", ["pdf", "fixed"])
+@pytest.mark.parametrize("kind", [0, 2])
+def test_rows_of_extreme_magnitude(rows, kind, tuning, monkeypatch):
+    """Rows scaled by 1e+-300 and 2^+-1000 on the built-in choices (warp kernel
+    for the small orders) and forced onto the block kernel: each kernel applies
+    the rows' scales once to an item's sum, so no product chain leaves the
+    double range; against the long-double oracle of the scaled matrices."""
+    monkeypatch.setenv("PERM_ROWS", rows)
+    if kind:
+        tuning(kind, L_cta=32)
+    ns = [5, 8, 11, 14, 17]
+    mats = []
+    for k, n in enumerate(ns):
+        A = W.complex_gaussian(n, 980 + k)
+        s = np.ones(n)
+        s[0], s[1], s[2], s[3] = 1e300, 1e-300, 2.0 ** 1000, 2.0 ** -1000
+        mats.append(A * s[:, None])
+    out, _ = _batch(mats)
+    _check_vs_oracle(out, ns, mats, every=1, n_max=17, what=f"extreme rows {rows} kind {kind}")
+
+
 def test_non_current_stream_without_pointer_tensor():
     """A batch launched on a stream other than the current one, with the
     pointer array and output made by the binding: results against the oracle

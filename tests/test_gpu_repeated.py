@@ -49,6 +49,23 @@ def test_vs_oracle_ryser2(mult):
     assert abs(got - ref) <= tol(n, ref, r[2]), (got, ref, float(r[2]))
 
 
+def test_rows_of_extreme_magnitude():
+    """Rows scaled by 1e+-300 and 2^+-1000: the products multiply unscaled row
+    values and the rows' scales are applied once per thread, so no product
+    chain leaves the double range; against the long-double oracle of the
+    scaled matrix (its range reaches 1e+-4932)."""
+    mult = [3, 1, 2, 2, 3]
+    n = sum(mult)
+    Cb = W.complex_gaussian(n, 331)[:, :len(mult)]
+    s = np.ones(n)
+    s[0], s[1], s[2], s[3] = 1e300, 1e-300, 2.0 ** 1000, 2.0 ** -1000
+    Cb = Cb * s[:, None]
+    r = O.per_repeated(Cb, mult)
+    ref = complex(float(r[0]), float(r[1]))
+    got = gpu_rep(Cb, mult)
+    assert abs(got - ref) <= tol(n, ref, r[2]), (got, ref, float(r[2]))
+
+
 @pytest.mark.parametrize("mult", [[3, 2, 2, 1, 4, 3, 2, 3, 2, 2], [1] * 18, [6, 6, 6, 4], [2] * 10])
 def test_vs_oracle_walk_of_expanded(mult):
     n = sum(mult)

@@ -36,6 +36,21 @@ def test_vs_oracle_sparse(n, p, seed):
     assert abs(got - ref) <= max(1e-10 * abs(ref), 8 * n * U * float(r[2])), (got, ref, float(r[2]))
 
 
+def test_rows_of_extreme_magnitude():
+    """Rows scaled by 1e+-300 and 2^+-1000 (the products multiply unscaled row
+    values, the rows' scales applied once per thread) against the long-double
+    oracle of the scaled matrix."""
+    n = 14
+    A = W.sparse_matrix(n, 0.2, 41)
+    s = np.ones(n)
+    s[0], s[1], s[2], s[3] = 1e300, 1e-300, 2.0 ** 1000, 2.0 ** -1000
+    A = A * s[:, None]
+    r = O.per_sparse(A)
+    ref = complex(float(r[0]), float(r[1]))
+    got = gpu_sparse(A)
+    assert abs(got - ref) <= max(1e-10 * abs(ref), 8 * n * U * float(r[2])), (got, ref, float(r[2]))
+
+
 @pytest.mark.parametrize("n,p,seed", [(20, 0.1, 7), (24, 0.08, 8)])
 def test_vs_glynn_oracle(n, p, seed):
     A = W.sparse_matrix(n, p, seed)
