@@ -1,7 +1,9 @@
 // Double-double helpers (device), written from the published error-free
 // transformations: Knuth's TwoSum and Dekker's FastTwoSum.  Only additions are
 // used, so FMA contraction cannot alter them.  Used for the per-thread
-// accumulator folds and the fixed-order reductions, never in the per-term path.
+// accumulator folds and the fixed-order reductions, never in the per-term path;
+// block and grid totals are summed exactly as 128-bit fixed-point integers
+// (fx128 below).
 #pragma once
 
 #include <cstdint>
@@ -54,6 +56,83 @@ __device__ __forceinline__ dd dd_warp_sum(dd a) {
 #pragma unroll
   for (int m = 16; m >= 1; m >>= 1) a = dd_add(a, dd_shfl_xor(a, m));
   return a;
+}
+
+// ---- Exact sums of double-double values on the integer pipes ----
+// A set of doubles is summed as signed 128-bit fixed-point integers in units
+// of 2^(emax - 1075 - kFxFrac), emax the largest biased exponent in the set
+// (at least 1).  Each double converts exactly apart from its bits below that
+// unit (below 2^-108 of the largest value); integer addition is exact and
+// associative, so the sum is the same for every order and tree, and no FP64
+// instruction runs until the one conversion back (a double-double tree would
+// issue 20 FP64 instructions per addition, on a pipe with 1/64 of the FP32
+// rate here).  Headroom: each value is below 2^(53 + kFxFrac) units and at
+// most 2^13 values are summed, so every partial sum stays below 2^122.
+constexpr int kFxFrac = 56;
+
+struct fx128 {
+  long long h;          // high 64 bits (signed)
+  unsigned long long l;  // low 64 bits
+};
+
+// Biased exponent field of a double (0 for zero and subnormals, 0x7FF for
+// infinities and NaN).
+__device__ __forceinline__ int dexp_field(double d) {
+  return (int)(((unsigned long long)__double_as_longlong(d) >> 52) & 0x7FFull);
+}
+
+// d in units of 2^(emax - 1075 - kFxFrac), magnitude truncated; requires
+// dexp_field(d) <= emax, 1 <= emax < 0x7FF.
+__device__ __forceinline__ fx128 fx128_of(double d, int emax) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
+  const int E = (int)((bits >> 52) & 0x7FFull);
+  unsigned long long M = bits & 0xFFFFFFFFFFFFFull;
+  int e = 1;  // subnormals: no implicit bit, the exponent of the smallest normal
+  if (E != 0) {
+    M |= 1ull << 52;
+    e = E;
+  }
+  const int sh = e - emax + kFxFrac;  // <= kFxFrac < 64
+  unsigned long long hi = 0, lo = 0;
+  if (sh > 0) {
+    lo = M << sh;
+    hi = M >> (64 - sh);
+  } else if (sh > -64) {
+    lo = M >> (-sh);
+  }
+  if (bits >> 63) {  // two's complement negation of (hi, lo)
+    lo = ~lo + 1ull;
+    hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+  }
+  return fx128{(long long)hi, lo};
+}
+
+__device__ __forceinline__ fx128 fx128_add(fx128 a, fx128 b) {
+  const unsigned long long l = a.l + b.l;
+  return fx128{a.h + b.h + (l < a.l ? 1ll : 0ll), l};
+}
+
+__device__ __forceinline__ fx128 fx128_warp_sum(fx128 a) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    const fx128 b{__shfl_xor_sync(0xffffffffu, a.h, m), __shfl_xor_sync(0xffffffffu, a.l, m)};
+    a = fx128_add(a, b);
+  }
+  return a;
+}
+
+// The fixed-point value v (units 2^(emax - 1075 - kFxFrac)) as a double-double:
+// v = h 2^64 + l split into four exact doubles (h rounded to 53 bits and its
+// remainder, the top 53 and the low 11 bits of l), summed in order.
+__device__ __forceinline__ dd dd_of_fx128(fx128 v, int emax) {
+  const double ph = __ll2double_rn(v.h);  // |v.h| < 2^58: the conversion back is exact
+  const long long rh = v.h - __double2ll_rn(ph);
+  dd r{ph * 0x1p64, 0.0};
+  r = dd_add_d(r, (double)rh * 0x1p64);
+  r = dd_add_d(r, __ull2double_rn(v.l & ~0x7FFull));
+  r = dd_add_d(r, __ull2double_rn(v.l & 0x7FFull));
+  const int sc = emax - 1075 - kFxFrac;
+  return dd{scalbn(r.hi, sc), scalbn(r.lo, sc)};
 }
 
 // +-1.0 from a bit, built with integer operations only (no FP64 instruction).

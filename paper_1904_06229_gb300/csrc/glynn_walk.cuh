@@ -252,23 +252,48 @@ __device__ __forceinline__ void block_store(dd accr, dd acci, dd* sRed, double* 
   block_store_to<CPLX>(accr, acci, sRed, partials + (size_t)blockIdx.x * (CPLX ? 4 : 2), accumulate);
 }
 
-// The same reduction, written to (or added into) the partial at o.
+// The same reduction, written to (or added into) the partial at o.  The
+// threads' double-double sums are added exactly as 128-bit fixed-point
+// integers (dd.cuh: fx128) on the integer pipes: the block's total does not
+// depend on the order of the threads, and the FP64 pipe (1/64 of the FP32
+// rate) converts only the one result.  A non-finite thread sum makes the
+// partial NaN (the status word already records the non-finite input).
 template <bool CPLX>
 __device__ __forceinline__ void block_store_to(dd accr, dd acci, dd* sRed, double* o, int accumulate) {
+  __shared__ int sEmax;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  accr = dd_warp_sum(accr);
-  if (CPLX) acci = dd_warp_sum(acci);
-  if (lane == 0) {
-    sRed[2 * warp] = accr;
-    sRed[2 * warp + 1] = acci;
+  if (threadIdx.x == 0) sEmax = 1;
+  __syncthreads();
+  int e = max(dexp_field(accr.hi), dexp_field(accr.lo));
+  if (CPLX) e = max(e, max(dexp_field(acci.hi), dexp_field(acci.lo)));
+  e = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+  if (lane == 0) atomicMax(&sEmax, e);
+  __syncthreads();
+  const int emax = sEmax;
+  fx128* sF = reinterpret_cast<fx128*>(sRed);  // two fx128 per warp: the 32 bytes of two dd
+  if (emax < 0x7FF) {
+    const fx128 fr = fx128_warp_sum(fx128_add(fx128_of(accr.hi, emax), fx128_of(accr.lo, emax)));
+    fx128 fi{0, 0};
+    if (CPLX) fi = fx128_warp_sum(fx128_add(fx128_of(acci.hi, emax), fx128_of(acci.lo, emax)));
+    if (lane == 0) {
+      sF[2 * warp] = fr;
+      sF[2 * warp + 1] = fi;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    dd tr = sRed[0], ti = sRed[1];
-    const int nw = blockDim.x >> 5;
-    for (int w = 1; w < nw; ++w) {
-      tr = dd_add(tr, sRed[2 * w]);
-      ti = dd_add(ti, sRed[2 * w + 1]);
+    dd tr, ti;
+    if (emax >= 0x7FF) {
+      tr = ti = dd{__longlong_as_double(0x7ff8000000000000ll), 0.0};
+    } else {
+      fx128 fr = sF[0], fi = sF[1];
+      const int nw = blockDim.x >> 5;
+      for (int w = 1; w < nw; ++w) {
+        fr = fx128_add(fr, sF[2 * w]);
+        fi = fx128_add(fi, sF[2 * w + 1]);
+      }
+      tr = dd_of_fx128(fr, emax);
+      ti = CPLX ? dd_of_fx128(fi, emax) : dd{0.0, 0.0};
     }
     if (accumulate) {
       tr = dd_add(tr, dd{o[0], o[1]});

@@ -44,10 +44,14 @@ struct FxShape {
   // that the threads of a warp read at once (each at its own Gray code) start
   // in different shared-memory banks.
   static constexpr int S = N | 1;
-  // +2A and -2A tables (int64, column-major), v0 (int64), per-row exponent bias (int), dd reduction slots
+  // +2A and -2A tables (int64, column-major), v0 (int64), two per-row int
+  // arrays (exponent biases sEb, scales sF); the kernel takes its pointers from
+  // these offsets.  The dd reduction slots reuse the tables after the walk.
   static constexpr size_t table_bytes = (size_t)N * S * E * sizeof(long long);
-  static constexpr size_t smem_bytes = 2 * table_bytes + (size_t)N * E * sizeof(long long) + N * sizeof(int) +
-                                       8 * sizeof(dd) + 16;
+  static constexpr size_t v0_off = 2 * table_bytes;
+  static constexpr size_t eb_off = v0_off + (size_t)N * E * sizeof(long long);
+  static constexpr size_t f_off = eb_off + (size_t)N * sizeof(int);
+  static constexpr size_t smem_bytes = f_off + (size_t)N * sizeof(int) + 8 * sizeof(dd) + 16;
 };
 
 // Double with value v * 2^(eb - 1086) (eb = 1086 - scale exponent), from the
@@ -563,13 +567,15 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk_fx(const double* __restri
                                                           int* __restrict__ status) {
   constexpr int E = CPLX ? 2 : 1;
   constexpr int S = FxShape<N, CPLX>::S;
+  using Shape = FxShape<N, CPLX>;
   extern __shared__ __align__(16) long long fsm[];
+  char* base = reinterpret_cast<char*>(fsm);
   long long* sP = fsm;
   long long* sM = sP + N * S * E;
-  long long* sV0 = sM + N * S * E;
-  int* sEb = reinterpret_cast<int*>(sV0 + N * E);
-  int* sF = sEb + N;
-  dd* sRed = reinterpret_cast<dd*>(fsm) ;  // reused after the walk (tables no longer read)
+  long long* sV0 = reinterpret_cast<long long*>(base + Shape::v0_off);
+  int* sEb = reinterpret_cast<int*>(base + Shape::eb_off);
+  int* sF = reinterpret_cast<int*>(base + Shape::f_off);
+  dd* sRed = reinterpret_cast<dd*>(fsm);  // reused after the walk (tables no longer read)
 
   const bool bad = fx_stage<N, CPLX>(A, sP, sM, sV0, sEb, sF, status);
 

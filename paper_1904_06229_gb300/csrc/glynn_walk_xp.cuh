@@ -344,6 +344,30 @@ __device__ __forceinline__ bool xp_stage_exact(const double* __restrict__ A, flo
   return false;
 }
 
+// Double-float pair (h, l) of v 2^-61 for an int64 v with |v| <= 2^62, with
+// integer and FP32 instructions only (the FP64 pipe runs at 1/64 of the FP32
+// rate on this part, and a re-seed converts every row).  v = a 2^46 + b 2^23 + c
+// with a = v >> 46 (signed, |a| <= 2^16) and b, c unsigned 23-bit fields.  Each
+// part is an exact float: a field placed in the significand of a power of two
+// P = 2^(23+k) (or added to 1.5 P, for the signed a) reads P + field 2^k
+// exactly, and subtracting P leaves field 2^k.  The parts do not overlap and
+// |a 2^-15| >= 2^-15 > b 2^-38 > c 2^-61 whenever the larger part is non-zero,
+// so two FastTwoSums (Dekker) sum them into a normalised pair; only the low
+// word's own addition rounds (about 2^-48 relative to v).
+__device__ __forceinline__ void pdf_split(long long v, float& h, float& l) {
+  const int a = (int)(v >> 46);
+  const unsigned b = (unsigned)((unsigned long long)v >> 23) & 0x7FFFFFu;
+  const unsigned c = (unsigned)v & 0x7FFFFFu;
+  const float fa = __fsub_rn(__int_as_float(0x43C00000 + a), 384.0f);               // 1.5 2^8, ulp 2^-15
+  const float fb = __fsub_rn(__int_as_float(0x38000000 | (int)b), 0x1p-15f);         // 2^-15, ulp 2^-38
+  const float fc = __fsub_rn(__int_as_float(0x2C800000 | (int)c), 0x1p-38f);         // 2^-38, ulp 2^-61
+  const float s = __fadd_rn(fa, fb);
+  const float e = __fsub_rn(fb, __fsub_rn(s, fa));
+  const float t = __fadd_rn(e, fc);
+  h = __fadd_rn(s, t);
+  l = __fsub_rn(t, __fsub_rn(h, s));
+}
+
 // Stage for double-float rows: Q_ij = rint(a_ij 2^(G_i + 61)) (|Q| <= 2^61),
 // the int64 columns 2 Q_ij (sQ, [k][j][lane] = (re, im): pair-major, so the
 // lanes of a warp re-seeding the same pair at different codes read entries
@@ -362,15 +386,14 @@ __device__ __forceinline__ bool xp_stage_df(const double* __restrict__ A, float4
     const int i = idx / N, j = idx - i * N;
     const int G = sG[i];
     const int k = i >> 1, lane = i & 1;
-    long long q2[2] = {0, 0};
+    long long q[2], q2[2] = {0, 0};
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
+      q[c] = __double2ll_rn(scalbn(A[(size_t)idx * 2 + c], G + kPdfGrid));
       float h = 0.f, l = 0.f;
       if (j < N - 1) {
-        q2[c] = 2 * __double2ll_rn(scalbn(A[(size_t)idx * 2 + c], G + kPdfGrid));
-        const double d = scalbn(__ll2double_rn(q2[c]), -kPdfGrid);
-        h = __double2float_rn(d);
-        l = __double2float_rn(d - (double)h);
+        q2[c] = 2 * q[c];
+        pdf_split(q2[c], h, l);
       }
       const size_t base = (((size_t)j * NP + k) * 2 + c) * 4;
       fP[base + lane] = h;
@@ -379,6 +402,7 @@ __device__ __forceinline__ bool xp_stage_df(const double* __restrict__ A, float4
       fM[base + 2 + lane] = -l;
     }
     sQ[((size_t)k * N + j) * 2 + lane] = make_longlong2(q2[0], q2[1]);
+    if (j == N - 1) sV0[k * 2 + lane] = make_longlong2(q[0], q[1]);  // Q_in, completed below
   }
   if (N & 1) {
     // the missing row of an odd order: constant 1 (seed 2^61, columns zero)
@@ -393,29 +417,20 @@ __device__ __forceinline__ bool xp_stage_df(const double* __restrict__ A, float4
     }
     if (threadIdx.x == 0) sV0[(NP - 1) * 2 + 1] = make_longlong2(1ll << kPdfGrid, 0);
   }
+  __syncthreads();
+  // seeds v0_i = Q_in - sum_{j<n} Q_ij from the int64 table (exact integer sums)
   if (threadIdx.x < N) {
-    const int i = threadIdx.x;
-    const int G = sG[i];
-    long long s[2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      s[c] = 0;
-      for (int j = 0; j < N; ++j) {
-        const long long q = __double2ll_rn(scalbn(A[((size_t)i * N + j) * 2 + c], G + kPdfGrid));
-        s[c] += (j == N - 1) ? q : -q;
-      }
+    const int i = threadIdx.x, k = i >> 1, lane = i & 1;
+    longlong2 s = sV0[k * 2 + lane];
+    for (int j = 0; j < N - 1; ++j) {
+      const longlong2 q2 = sQ[((size_t)k * N + j) * 2 + lane];
+      s.x -= q2.x >> 1;
+      s.y -= q2.y >> 1;
     }
-    sV0[(i >> 1) * 2 + (i & 1)] = make_longlong2(s[0], s[1]);
+    sV0[k * 2 + lane] = s;
   }
   __syncthreads();
   return false;
-}
-
-// Double-float pair (h, l) of v 2^-61 for an int64 v.
-__device__ __forceinline__ void pdf_split(long long v, float& h, float& l) {
-  const double d = __ll2double_rn(v) * 0x1p-61;
-  h = __double2float_rn(d);
-  l = __double2float_rn(d - (double)h);
 }
 
 // Re-seed every row pair from its exact int64 value at code r (App. A steps

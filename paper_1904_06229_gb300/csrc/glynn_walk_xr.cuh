@@ -107,11 +107,10 @@ __device__ __forceinline__ bool xr_stage_df(const double* __restrict__ A, float4
     const int k = i >> 1, lane = i & 1;
     float h = 0.f, l = 0.f;
     long long q2 = 0;
+    const long long q = __double2ll_rn(scalbn(A[idx], sG[i] + kPdfGrid));
     if (j < N - 1) {
-      q2 = 2 * __double2ll_rn(scalbn(A[idx], sG[i] + kPdfGrid));
-      const double d = scalbn(__ll2double_rn(q2), -kPdfGrid);
-      h = __double2float_rn(d);
-      l = __double2float_rn(d - (double)h);
+      q2 = 2 * q;
+      pdf_split(q2, h, l);
     }
     const size_t base = ((size_t)j * NP + k) * 4;
     fP[base + lane] = h;
@@ -119,6 +118,7 @@ __device__ __forceinline__ bool xr_stage_df(const double* __restrict__ A, float4
     fM[base + lane] = -h;
     fM[base + 2 + lane] = -l;
     q64[((size_t)k * N + j) * 2 + lane] = q2;
+    if (j == N - 1) reinterpret_cast<long long*>(sV0)[k * 2 + lane] = q;  // Q_in, completed below
   }
   long long* v64 = reinterpret_cast<long long*>(sV0);
   if (N & 1) {
@@ -131,14 +131,13 @@ __device__ __forceinline__ bool xr_stage_df(const double* __restrict__ A, float4
     }
     if (threadIdx.x == 0) v64[(NP - 1) * 2 + 1] = 1ll << kPdfGrid;
   }
+  __syncthreads();
+  // seeds v0_i = Q_in - sum_{j<n} Q_ij from the int64 table (exact integer sums)
   if (threadIdx.x < N) {
-    const int i = threadIdx.x;
-    long long s = 0;
-    for (int j = 0; j < N; ++j) {
-      const long long q = __double2ll_rn(scalbn(A[(size_t)i * N + j], sG[i] + kPdfGrid));
-      s += (j == N - 1) ? q : -q;
-    }
-    v64[(i >> 1) * 2 + (i & 1)] = s;
+    const int i = threadIdx.x, k = i >> 1, lane = i & 1;
+    long long s = v64[k * 2 + lane];
+    for (int j = 0; j < N - 1; ++j) s -= q64[((size_t)k * N + j) * 2 + lane] >> 1;
+    v64[k * 2 + lane] = s;
   }
   __syncthreads();
   return false;

@@ -23,33 +23,59 @@
 
 namespace perm {
 
-// ---- fixed-order reduction of per-block dd partials (App. A "permanent":
+// ---- reduction of per-block dd partials (App. A "permanent":
 // S = 2 (-1)^n sum_k S_k with the partials kept in an array, Sec. 2.B) ----
+// The partials are added exactly as 128-bit fixed-point integers (dd.cuh:
+// fx128), so the total does not depend on the order of the blocks and the
+// FP64 pipe converts only the one result.  At most kFinMaxParts partials
+// (2 doubles each per component: within the 2^13-value headroom).
 constexpr int kFinThreads = 256;
+constexpr int kFinMaxParts = 4096;
 
 __global__ void __launch_bounds__(kFinThreads) k_finalize(const double* __restrict__ partials, int nparts, int cplx,
                                                           int n, int mode, double* __restrict__ out) {
-  __shared__ dd sRed[2 * (kFinThreads / 32)];
+  __shared__ fx128 sF[2 * (kFinThreads / 32)];
+  __shared__ int sEmax;
   const int stride = cplx ? 4 : 2;
-  dd ar{0.0, 0.0}, ai{0.0, 0.0};
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) sEmax = 1;
+  __syncthreads();
+  int e = 0;
   for (int k = threadIdx.x; k < nparts; k += kFinThreads) {
     const double* p = partials + (size_t)k * stride;
-    ar = dd_add(ar, dd{p[0], p[1]});
-    if (cplx) ai = dd_add(ai, dd{p[2], p[3]});
+    for (int q = 0; q < stride; ++q) e = max(e, dexp_field(p[q]));
   }
-  ar = dd_warp_sum(ar);
-  ai = dd_warp_sum(ai);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    sRed[2 * warp] = ar;
-    sRed[2 * warp + 1] = ai;
+  e = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+  if (lane == 0) atomicMax(&sEmax, e);
+  __syncthreads();
+  const int emax = sEmax;
+  if (emax < 0x7FF) {
+    fx128 fr{0, 0}, fi{0, 0};
+    for (int k = threadIdx.x; k < nparts; k += kFinThreads) {
+      const double* p = partials + (size_t)k * stride;
+      fr = fx128_add(fr, fx128_add(fx128_of(p[0], emax), fx128_of(p[1], emax)));
+      if (cplx) fi = fx128_add(fi, fx128_add(fx128_of(p[2], emax), fx128_of(p[3], emax)));
+    }
+    fr = fx128_warp_sum(fr);
+    fi = fx128_warp_sum(fi);
+    if (lane == 0) {
+      sF[2 * warp] = fr;
+      sF[2 * warp + 1] = fi;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    dd tr = sRed[0], ti = sRed[1];
-    for (int w = 1; w < kFinThreads / 32; ++w) {
-      tr = dd_add(tr, sRed[2 * w]);
-      ti = dd_add(ti, sRed[2 * w + 1]);
+    dd tr, ti;
+    if (emax >= 0x7FF) {
+      tr = ti = dd{__longlong_as_double(0x7ff8000000000000ll), 0.0};
+    } else {
+      fx128 fr = sF[0], fi = sF[1];
+      for (int w = 1; w < kFinThreads / 32; ++w) {
+        fr = fx128_add(fr, sF[2 * w]);
+        fi = fx128_add(fi, sF[2 * w + 1]);
+      }
+      tr = dd_of_fx128(fr, emax);
+      ti = dd_of_fx128(fi, emax);
     }
     if (mode == 0 || mode == 2 || mode == 3) {
       // mode 0: per = 2 (-1)^(n-1) * sum (halved Glynn form)
@@ -75,6 +101,7 @@ void preload_abi_kernels() { load_kernel(k_finalize); }
 
 cudaError_t finalize_launch(const double* partials, int nparts, bool cplx, int n, int mode, double* out,
                             cudaStream_t stream) {
+  if (nparts < 1 || nparts > kFinMaxParts) return cudaErrorInvalidValue;
   k_finalize<<<1, kFinThreads, 0, stream>>>(partials, nparts, cplx ? 1 : 0, n, mode, out);
   return cudaGetLastError();
 }

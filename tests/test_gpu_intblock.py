@@ -115,3 +115,27 @@ def test_unequal_entries_within_a_row(n, rows):
     re, im, asum = O.per(B)
     ref = complex(float(re), float(im))
     T.check(gpu_c128(B), ref, float(asum), n, T.unit(rows), f"unequal entries n={n}")
+
+
+@pytest.mark.parametrize("n", [7, 9, 12])
+def test_short_reseed_period_keeps_seed_precision(n, monkeypatch):
+    """PERM_PDF_TILE_LOG=4: every row is re-seeded from its exact int64 value
+    every 16 codes, so the conversion of the int64 seeds to double-float pairs
+    (integer fields placed in FP32 significands, summed by FastTwoSum) sets the
+    error.  It must stay at the double-float unit: |err| <= 8 n 2^-48 sum|t|.
+    A dropped or misplaced 23-bit field of the conversion errs by about 2^-36
+    per factor, which this bound rejects at these orders (few terms to average
+    the error out).  Complex and real walks."""
+    monkeypatch.setenv("PERM_PDF_TILE_LOG", "4")
+    A = W.complex_gaussian(n, 990 + n)
+    re, im, asum = O.per(A)
+    err = abs(gpu_c128(A) - complex(float(re), float(im)))
+    print(f"tile 16, complex n={n}: |err| / sum|t| = {err / float(asum):.3e}")
+    assert err <= 8 * n * 2.0 ** -48 * float(asum)
+    R = W.real_gaussian(n, 991 + n)
+    re, _, asum = O.per(R)
+    out = P.perm_f64(torch.from_numpy(R).cuda()).cpu().numpy()
+    assert P.perm_last_status() == 0
+    err = abs(float(out[0]) - float(re))
+    print(f"tile 16, real n={n}: |err| / sum|t| = {err / float(asum):.3e}")
+    assert err <= 8 * n * 2.0 ** -48 * float(asum)
