@@ -205,6 +205,22 @@ __device__ __forceinline__ double signed_pow2(int E, uint32_t negative) {
   return __hiloint2double((int)(((uint32_t)(1023 + E) << 20) | (negative << 31)), 0);
 }
 
+// (-1)^negative f 2^E as a double, built from the bits of the float f with
+// integer instructions only (the FP64 pipe, at 1/64 of the FP32 rate here,
+// would convert it): sign flipped, exponent field re-biased from 127 to 1023
+// plus E, the 23 fraction bits moved to the top of the 52.  Exact.  Zero and
+// subnormal floats, and results below the normal double range, give zero (a
+// term part below 2^-1022 of the permanent's scale).  E must not take the
+// result above the double range.
+__device__ __forceinline__ double f32_scaled_f64(float f, int E, uint32_t negative) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t mag = u & 0x7FFFFFFFu;
+  const int be = (int)(mag >> 23) + 896 + E;  // biased double exponent
+  const uint32_t hi = ((u ^ (negative << 31)) & 0x80000000u) | ((mag >> 3) + ((uint32_t)(896 + E) << 20));
+  const bool zero = mag < 0x00800000u || be <= 0;
+  return __hiloint2double(zero ? 0 : (int)hi, zero ? 0 : (int)(u << 29));
+}
+
 // Product of the N row sums (NP packed pairs) as FP64 parts scaled by
 // 2^E: on return p = (pr_hi + pr_lo) + i (pi_hi + pi_lo) times 2^E.
 template <int N>
@@ -497,11 +513,10 @@ __device__ __forceinline__ void xp_term(const P4 (&v)[kPairs<N>], uint32_t odd, 
   cdf z;
   int E;
   xp_product<N>(v, z, E);
-  const double s2 = signed_pow2(E, odd);
-  sr = fma((double)z.rh, s2, sr);
-  sr = fma((double)z.rl, s2, sr);
-  si = fma((double)z.ih, s2, si);
-  si = fma((double)z.il, s2, si);
+  sr += f32_scaled_f64(z.rh, E, odd);
+  sr += f32_scaled_f64(z.rl, E, odd);
+  si += f32_scaled_f64(z.ih, E, odd);
+  si += f32_scaled_f64(z.il, E, odd);
 }
 
 // Exact float-pair rows: seeded once, then per code the product, the signed

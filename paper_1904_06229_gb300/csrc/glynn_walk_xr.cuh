@@ -187,10 +187,9 @@ __device__ __forceinline__ void thread_walk_xr_df(const float4* __restrict__ sP,
       float zh, zl;
       int E;
       xr_product<N>(v, zh, zl, E);
-      const double s2 = signed_pow2(E, odd);
+      s += f32_scaled_f64(zh, E, odd);
+      s += f32_scaled_f64(zl, E, odd);
       odd ^= 1u;
-      s = fma((double)zh, s2, s);
-      s = fma((double)zl, s2, s);
       int j;
       uint32_t neg;
       gray_step(r, j, neg);
