@@ -64,7 +64,11 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "configs.json")
 # kernel (profiles/k_walk_xp_pdf_c128_n40_haar.md); the issue-slot fraction
 # below divides it by the scheduler rate of 4 warp instructions per clock
 # per SM at the SM clock sampled during the run.
-ISSUED_LANE_INSTR_PER_CODE_N40 = 1252
+ISSUED_LANE_INSTR_PER_CODE_N40 = 1265
+# DRAM bytes (read + write) of one launch of that kernel at n = 40, from the
+# same capture: the per-block staging of the 25.6 KB matrix, the partials and
+# write-backs of the L2 flush buffer; independent of the codes per launch.
+DRAM_BYTES_PER_LAUNCH_N40 = 102912 + 732672
 
 
 def workload_matrix(n=N_ORDER, seed=SEED):
@@ -265,13 +269,15 @@ def roofline_of(rows, n, codes, launch_s, peaks, sms, clk_mhz):
         achieved = codes * ops / launch_s / 1e9
         peak = 2.0 * peaks["ffma2"]  # packed FMA: two FP32 operations per lane instruction
         out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP32 lane-op/s",
-               "frac": achieved / peak, "traffic": None,
+               "frac": achieved / peak,
+               "traffic": DRAM_BYTES_PER_LAUNCH_N40 if n == N_ORDER else None,
                "kernel": f"perm::k_walk_xp<{n}, false> (packed double-float rows and products, f32x2 FMA pipe)",
                "rows": rows, "fp32_ops_per_term": ops,
                "peak_source": "measured this run: perm_pipe_peak(FFMA2) x 2 FP32 operations (MEASURED_PEAKS.json has "
                               "no FP32 figure)",
-               "traffic_note": "the walk reads its 25.6 KB matrix once per block; ncu measured 0.15 MB read + 11.8 MB "
-                               "written per 2^30-code launch (profiles/), independent of the codes per launch"}
+               "traffic_note": "bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, ncu, one 2^30-code "
+                               "launch of the same kernel: 0.10 MB read + 0.73 MB written); the walk reads its 25.6 KB "
+                               "matrix once per block, so the traffic does not grow with the codes per launch"}
         if n == N_ORDER and clk_mhz:
             ipc = ISSUED_LANE_INSTR_PER_CODE_N40
             out["issue_frac"] = codes * ipc / launch_s / (128.0 * sms * clk_mhz * 1e6)
