@@ -242,8 +242,8 @@ __device__ __forceinline__ void stage(const double* __restrict__ A, double* sA, 
   __syncthreads();
 }
 
-// Block-level fixed-order reduction of per-thread dd sums; thread 0 writes
-// (or adds into) this block's slot of `partials`.
+// Block-level exact reduction of per-thread dd sums; thread 0 writes (or adds
+// into) this block's slot of `partials`.
 template <bool CPLX>
 __device__ __forceinline__ void block_store_to(dd accr, dd acci, dd* sRed, double* o, int accumulate);
 
