@@ -464,7 +464,7 @@ def extras(args, line, P, torch, dev, dA, A, rows, peaks, stream, slice_first):
     if args.batch_sample > 0:
         line["batch"] = batch_measure(P, torch, dev, args.batch_sample)
     if args.batch_study > 0:
-        line["batch_study"] = batch_study_measure(P, torch, dev, args.batch_study)
+        line["batch_study"] = batch_study_measure(P, torch, dev, args.batch_study, peaks)
     if not args.no_cpu_baseline:
         cpu_leg(line, P, torch, dev, dA, A)
 
@@ -718,11 +718,15 @@ def batch_measure(P, torch, dev, sample):
             "max_abs_diff_vs_per_launch": d, "max_abs_value": scale, "gpu_launches_batched": 2}
 
 
-def batch_study_measure(P, torch, dev, count):
+def batch_study_measure(P, torch, dev, count, peaks=None):
     """The whole batch study in one persistent launch: `count` matrices (n ~
     U{12..28}, half Gaussian, half Haar S(n^2, n), shuffled; seed 3) through
     perm_batch_stats, with the per-order moments of X = |per| / sqrt(n!), and
-    64 results checked against single perm_c128 launches."""
+    64 results checked against single perm_c128 launches.  Roofline: the FP32
+    lane operations of the orders on the block-per-item kernels (the default
+    walk's arithmetic, pdf_fp32_ops per code) over the launch time, against
+    the measured packed-FMA rate; the orders on the warp kernel (FP64 or
+    fixed-point rows) are left out of the count and named."""
     from paper_1904_06229_gb300 import workloads as W
 
     t0 = time.time()
@@ -761,10 +765,27 @@ def batch_study_measure(P, torch, dev, count):
         if c > 0:
             per_n[str(n)] = {"count": int(c), "mean_X": st[n, 1] / c, "mean_X2": st[n, 2] / c, "mean_X4": st[n, 4] / c}
     kernel_s = total_s - plan_s
-    return {"matrices": count, "orders": "12..28", "terms": terms, "generate_s": gen_s,
-            "seconds_incl_host_plan": total_s, "host_plan_s": plan_s, "perms_per_s": count / kernel_s,
-            "terms_per_s": terms / kernel_s, "status": status, "max_rel_diff_vs_perm_c128_64": worst,
-            "per_order": per_n}
+    out = {"matrices": count, "orders": "12..28", "terms": terms, "generate_s": gen_s,
+           "seconds_incl_host_plan": total_s, "host_plan_s": plan_s, "perms_per_s": count / kernel_s,
+           "terms_per_s": terms / kernel_s, "status": status, "max_rel_diff_vs_perm_c128_64": worst,
+           "per_order": per_n}
+    if peaks:
+        _, kinds = P.perm_batch_tuning(torch.cuda.current_device())
+        ops, warp_orders, warp_terms = 0, [], 0
+        for n in np.unique(ns):
+            codes = int((ns == n).sum()) << (int(n) - 1)
+            if kinds[int(n)] in (2, 3, 4):
+                ops += codes * pdf_fp32_ops(int(n))
+            else:
+                warp_orders.append(int(n))
+                warp_terms += codes
+        achieved = ops / kernel_s / 1e9
+        peak = 2.0 * peaks["ffma2"]
+        out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP32 lane-op/s",
+                           "frac": achieved / peak, "fp32_lane_ops": ops,
+                           "warp_kernel_orders": warp_orders, "warp_kernel_terms_share": warp_terms / terms,
+                           "peak_source": "perm_pipe_peak(FFMA2) x 2, measured this run"}
+    return out
 
 
 def main():
