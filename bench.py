@@ -69,6 +69,10 @@ ISSUED_LANE_INSTR_PER_CODE_N40 = 1265
 # same capture: the per-block staging of the 25.6 KB matrix, the partials and
 # write-backs of the L2 flush buffer; independent of the codes per launch.
 DRAM_BYTES_PER_LAUNCH_N40 = 102912 + 732672
+# Lane instructions per code of the exact modular kernel k_mod<36> (0-1,
+# n = 36, exact per-thread 256-bit sums), from ncu on one whole launch
+# (profiles/k_mod_n36_zero_one.md); an integer-issue-bound kernel.
+ISSUED_LANE_INSTR_PER_CODE_MOD36 = 170
 
 
 def workload_matrix(n=N_ORDER, seed=SEED):
@@ -457,7 +461,8 @@ def extras(args, line, P, torch, dev, dA, A, rows, peaks, stream, slice_first):
     if not args.no_extras:
         line["n48"] = n48_measure(P, torch, dev)
         line["c1_n20"] = c1_measure(P, torch, dev)
-        line["exact"] = exact_measure(P, torch, dev)
+        clk = (line.get("clocks") or {}).get("sm_mhz")
+        line["exact"] = exact_measure(P, torch, dev, clk)
         line["precision"] = precision_measure(P, torch, dev)
         line["next_rows"] = next_rows_measure(P, torch, dev)
         line["stats"] = stats_measure(P, torch, dev)
@@ -531,11 +536,13 @@ def c1_measure(P, torch, dev):
             "value": [float(v[0]), float(v[1])]}
 
 
-def exact_measure(P, torch, dev):
+def exact_measure(P, torch, dev, clk_mhz=None):
     """Exact 0-1 permanents (density 1/2; n = 30 seed 6, n = 36 seed 7) modulo
     four 62-bit primes, CRT on the host; each checked bit for bit against the
     stored oracle value (tests/golden/configs.json), also through the
-    modular group walk."""
+    modular group walk.  n = 36 carries the issue-slot roofline of its
+    integer kernel (ncu's lane instructions per code x codes/s over 4 warp
+    instructions per clock per SM at the SM clock sampled in the run)."""
     from paper_1904_06229_gb300 import workloads as W
 
     golden = load_golden()
@@ -561,6 +568,14 @@ def exact_measure(P, torch, dev):
                         "per_bits": val.bit_length(), "matches_oracle": val == ref,
                         "modular_walk": {"seconds": sec_m, "codes_per_s": (1 << (n - 1)) / sec_m,
                                          "same_residues": res_m.cpu().tolist() == res.cpu().tolist()}}
+        if n == 36 and clk_mhz:
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            achieved = (1 << (n - 1)) / sec * ISSUED_LANE_INSTR_PER_CODE_MOD36 / 1e9
+            peak = 128.0 * sms * clk_mhz * 1e6 / 1e9
+            out[f"n{n}"]["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak,
+                                        "unit": "G lane-instr/s (issue slots)", "frac": achieved / peak,
+                                        "issued_lane_instr_per_code": ISSUED_LANE_INSTR_PER_CODE_MOD36,
+                                        "kernel": "perm::k_mod<36> (int32 rows, exact 256-bit per-thread sums)"}
     return out
 
 
