@@ -6,10 +6,12 @@
 // registers per row pair instead of 8, a step's update is one double-float
 // add (11 packed operations) per pair, and a product step is an exact FP32
 // product by FMA with its two cross terms (4 packed operations, low part left
-// unrenormalised).  Eight chains in four packed chain pairs, power-of-two
-// renormalisation every eight factors and at the end; the lanes are joined by
-// one scalar double-float product and the term is rebuilt as FP64 like the
-// complex walk's.  Re-seeds from exact int64 rows every 2^tile_log codes as
+// unrenormalised).  Six chains in three packed chain pairs (measured against
+// two, four and five pairs at n = 32, 36, 40: three is 4-6 % faster than four
+// at every order; two wins only at n = 32), power-of-two renormalisation every
+// eight factors and at the end; the lanes are joined by one scalar
+// double-float product and the term is rebuilt as FP64 like the complex
+// walk's.  Re-seeds from exact int64 rows every 2^tile_log codes as
 // in the complex walk.
 #pragma once
 
@@ -27,7 +29,7 @@ struct XrShape {
   static constexpr size_t smem_bytes = 2 * table_f4 * sizeof(float4) + seed_bytes + 8 * sizeof(dd) + 16;
 };
 
-constexpr int kXrChainPairs = 4;
+constexpr int kXrChainPairs = 3;
 
 // Two real double-float numbers side by side (lanes .x and .y).
 struct P2 {
