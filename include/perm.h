@@ -245,7 +245,11 @@ int perm_batch_plans(int* built);
  *       b = 0: X < 1e-4;  b = 1..96: 10^(-4+(b-1)/16) <= X < 10^(-4+b/16);
  *       b = 97: X >= 100.
  * stats: DEVICE array of 33 * PERM_STATS_STRIDE doubles (overwritten).
- * Sums are formed in a fixed order (deterministic); counts are exact. */
+ * Chunks of 4096 results per block, then one block per order: the moment sums
+ * are exact 128-bit fixed-point integer sums of per-thread FP64 sums (the same
+ * value whatever the block order), counts are exact.  Per-call scratch of
+ * about 450 bytes per chunk, stream-ordered.  10^7 results of one order take
+ * about 1.5 ms on GB300. */
 #define PERM_STATS_STRIDE 103
 int perm_batch_stats(const double* const* ptrs, const int* ns, int count, double* out, double* stats, void* stream);
 

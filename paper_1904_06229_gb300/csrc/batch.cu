@@ -223,76 +223,155 @@ __global__ void k_set_args(BatchArgs* __restrict__ ba, const double* const* ptrs
 // stats[n * PERM_STATS_STRIDE + ...]: [0] count, [1..4] sum X^1..X^4,
 // [5 + b] histogram: b = 0 for X < 1e-4, b = 1..96 for
 // 10^(-4 + (b-1)/16) <= X < 10^(-4 + b/16) (16 bins per decade), b = 97 for
-// X >= 100.  One block per order, over that order's positions; every sum is
-// formed in a fixed order (double-double per thread, fixed tree), counts are
-// integer atomics.
+// X >= 100.  Two kernels: one block per chunk of kStatsChunk positions of one
+// order writes the chunk's four moment sums (each thread's FP64 sums added
+// exactly as 128-bit fixed-point integers over the block) and its histogram;
+// then one block per order adds its chunks' records, the moments again as
+// exact integer sums, the counts as integers.  Every total is independent of
+// the order in which blocks and threads finish.
 constexpr int kStatsEdges = 97;  // 10^(-4 + j/16), j = 0..96
 constexpr int kStatsStride = 5 + kStatsEdges + 1;
+constexpr int kStatsBins = kStatsEdges + 1;
+constexpr int kStatsChunk = 4096;  // positions per block of the first kernel
+constexpr int kStatsThreads = 256;
 
 struct StatsParams {
   double inv_sqrt_fact[kBatchNMax + 1];
   double edges[kStatsEdges];
+  int cfirst[kBatchNMax + 2];  // chunks of order m: [cfirst[m], cfirst[m + 1])
 };
 
-__global__ void __launch_bounds__(256)
-    k_batch_stats(const BatchArgs* __restrict__ ba, const int* __restrict__ perm, const __grid_constant__ BatchTable tab,
-                  StatsParams sp, double* __restrict__ stats) {
-  const int n = blockIdx.x;
-  __shared__ unsigned int hist[kStatsEdges + 1];
-  __shared__ unsigned int cnt;
-  __shared__ dd red[4 * 8];
-  for (int b = threadIdx.x; b <= kStatsEdges; b += blockDim.x) hist[b] = 0;
-  if (threadIdx.x == 0) cnt = 0;
-  __syncthreads();
-  dd m1{0, 0}, m2{0, 0}, m3{0, 0}, m4{0, 0};
-  unsigned int c = 0;
-  const double* out = ba->out;
-  const int lo_pos = n >= 1 && tab.kind[n] != kBatchNone ? tab.mstart[n] : 0;
-  const int hi_pos = n >= 1 && tab.kind[n] != kBatchNone ? tab.mstart[n] + tab.mcount[n] : 0;
-  for (int i = lo_pos + (int)threadIdx.x; i < hi_pos; i += blockDim.x) {
-    const int k = perm[i];
-    const double re = out[2 * (size_t)k], im = out[2 * (size_t)k + 1];
-    const double x = sqrt(re * re + im * im) * sp.inv_sqrt_fact[n];
-    const double x2 = x * x;
-    m1 = dd_add_d(m1, x);
-    m2 = dd_add_d(m2, x2);
-    m3 = dd_add_d(m3, x2 * x);
-    m4 = dd_add_d(m4, x2 * x2);
-    ++c;
-    // bin = number of edges <= x (binary search over the ascending edges)
-    int lo = 0, hi = kStatsEdges;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (sp.edges[mid] <= x)
-        lo = mid + 1;
-      else
-        hi = mid;
-    }
-    atomicAdd(&hist[lo], 1u);
-  }
-  m1 = dd_warp_sum(m1);
-  m2 = dd_warp_sum(m2);
-  m3 = dd_warp_sum(m3);
-  m4 = dd_warp_sum(m4);
-  for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+// Exact sums over the block of K per-thread doubles (dd.cuh: fx128); the
+// totals, as double-doubles, on thread 0 (NaN if any value is non-finite).
+template <int K>
+__device__ __forceinline__ void block_sum_exact(const double (&v)[K], dd (&tot)[K]) {
+  __shared__ int sEmax;
+  __shared__ fx128 sF[K * (kStatsThreads / 32)];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    red[4 * warp] = m1;
-    red[4 * warp + 1] = m2;
-    red[4 * warp + 2] = m3;
-    red[4 * warp + 3] = m4;
-    atomicAdd(&cnt, c);
+  if (threadIdx.x == 0) sEmax = 1;
+  __syncthreads();
+  int e = 0;
+#pragma unroll
+  for (int q = 0; q < K; ++q) e = max(e, dexp_field(v[q]));
+  e = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+  if (lane == 0) atomicMax(&sEmax, e);
+  __syncthreads();
+  const int emax = sEmax;
+  if (emax < 0x7FF) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const fx128 f = fx128_warp_sum(fx128_of(v[q], emax));
+      if (lane == 0) sF[K * warp + q] = f;
+    }
   }
   __syncthreads();
-  double* st = stats + (size_t)n * kStatsStride;
   if (threadIdx.x == 0) {
-    dd t[4] = {red[0], red[1], red[2], red[3]};
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-      for (int q = 0; q < 4; ++q) t[q] = dd_add(t[q], red[4 * w + q]);
-    st[0] = (double)cnt;
-    for (int q = 0; q < 4; ++q) st[1 + q] = __dadd_rn(t[q].hi, t[q].lo);
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      if (emax >= 0x7FF) {
+        tot[q] = dd{__longlong_as_double(0x7ff8000000000000ll), 0.0};
+        continue;
+      }
+      fx128 f = sF[q];
+      for (int w = 1; w < kStatsThreads / 32; ++w) f = fx128_add(f, sF[K * w + q]);
+      tot[q] = dd_of_fx128(f, emax);
+    }
   }
-  for (int b = threadIdx.x; b <= kStatsEdges; b += blockDim.x) st[5 + b] = (double)hist[b];
+}
+
+// Order of chunk c (0 if none).
+__device__ __forceinline__ int stats_order_of(const StatsParams& sp, int c) {
+  for (int m = 1; m <= kBatchNMax; ++m)
+    if (c >= sp.cfirst[m] && c < sp.cfirst[m + 1]) return m;
+  return 0;
+}
+
+// One block per chunk: moments (as double-double hi, lo pairs) to cmom[8 c ..],
+// histogram to chist[kStatsBins c ..].
+__global__ void __launch_bounds__(kStatsThreads)
+    k_batch_stats_part(const BatchArgs* __restrict__ ba, const int* __restrict__ perm,
+                       const __grid_constant__ BatchTable tab, const __grid_constant__ StatsParams sp,
+                       double* __restrict__ cmom, unsigned int* __restrict__ chist) {
+  __shared__ unsigned int hist[kStatsBins];
+  const int c = blockIdx.x;
+  const int n = stats_order_of(sp, c);
+  for (int b = threadIdx.x; b < kStatsBins; b += blockDim.x) hist[b] = 0;
+  __syncthreads();
+  double m[4] = {0.0, 0.0, 0.0, 0.0};
+  if (n > 0) {
+    const int lo_pos = tab.mstart[n] + (c - sp.cfirst[n]) * kStatsChunk;
+    const int hi_pos = min(lo_pos + kStatsChunk, tab.mstart[n] + tab.mcount[n]);
+    const double* out = ba->out;
+    for (int i = lo_pos + (int)threadIdx.x; i < hi_pos; i += blockDim.x) {
+      const int k = perm[i];
+      const double re = out[2 * (size_t)k], im = out[2 * (size_t)k + 1];
+      const double x = sqrt(re * re + im * im) * sp.inv_sqrt_fact[n];
+      const double x2 = x * x;
+      m[0] += x;
+      m[1] += x2;
+      m[2] += x2 * x;
+      m[3] += x2 * x2;
+      // bin = number of edges <= x (binary search over the ascending edges)
+      int lo = 0, hi = kStatsEdges;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (sp.edges[mid] <= x)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      atomicAdd(&hist[lo], 1u);
+    }
+  }
+  dd tot[4];
+  block_sum_exact<4>(m, tot);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      cmom[8 * (size_t)c + 2 * q] = tot[q].hi;
+      cmom[8 * (size_t)c + 2 * q + 1] = tot[q].lo;
+    }
+  }
+  for (int b = threadIdx.x; b < kStatsBins; b += blockDim.x) chist[(size_t)kStatsBins * c + b] = hist[b];
+}
+
+// One block per order: its chunks' records added (moments exactly, counts as
+// integers) into stats[n * kStatsStride ..]; zeros for an order not in the batch.
+__global__ void __launch_bounds__(kStatsThreads)
+    k_batch_stats_final(const __grid_constant__ BatchTable tab, const __grid_constant__ StatsParams sp,
+                        const double* __restrict__ cmom, const unsigned int* __restrict__ chist,
+                        double* __restrict__ stats) {
+  const int n = blockIdx.x;
+  const int c0 = n >= 1 ? sp.cfirst[n] : 0, c1 = n >= 1 ? sp.cfirst[n + 1] : 0;
+  double* st = stats + (size_t)n * kStatsStride;
+  // histogram: one thread per bin, chunks in order (integer sums)
+  for (int b = threadIdx.x; b < kStatsBins; b += blockDim.x) {
+    unsigned long long h = 0;
+    for (int c = c0; c < c1; ++c) h += chist[(size_t)kStatsBins * c + b];
+    st[5 + b] = (double)h;
+  }
+  // moments: every thread's share of the chunks' hi and lo parts, summed exactly
+  double part[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) part[q] = 0.0;
+  // each thread takes at most one chunk per pass; a pass is summed exactly,
+  // the passes are added in order in double-double
+  dd acc[4] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+  for (int base = c0; base < c1; base += blockDim.x) {
+    const int c = base + (int)threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) part[q] = c < c1 ? cmom[8 * (size_t)c + q] : 0.0;
+    dd t[8];
+    block_sum_exact<8>(part, t);
+    if (threadIdx.x == 0)
+      for (int q = 0; q < 4; ++q) acc[q] = dd_add(acc[q], dd_add(t[2 * q], t[2 * q + 1]));
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    st[0] = n >= 1 && tab.kind[n] != kBatchNone ? (double)tab.mcount[n] : 0.0;
+    for (int q = 0; q < 4; ++q) st[1 + q] = __dadd_rn(acc[q].hi, acc[q].lo);
+  }
 }
 
 template <int ROWS>
@@ -342,7 +421,8 @@ cudaError_t batch_launch_cta(int kind, const BatchArgs* ba, const int* perm, con
 
 void preload_batch_kernels() {
   load_kernel(k_batch_finalize);
-  load_kernel(k_batch_stats);
+  load_kernel(k_batch_stats_part);
+  load_kernel(k_batch_stats_final);
   load_kernel(k_upload);
   load_kernel(k_set_args);
   batch_resident_blocks_rows(kRowsF64);
@@ -782,9 +862,31 @@ static int batch_run(const double* const* ptrs, const int* ns, int count, double
     sp.inv_sqrt_fact[n] = 1.0 / std::sqrt(f);
   }
   for (int j = 0; j < kStatsEdges; ++j) sp.edges[j] = std::pow(10.0, -4.0 + (double)j / 16.0);
-  k_batch_stats<<<kBatchNMax + 1, 256, 0, s>>>((const BatchArgs*)plan->args, (const int*)plan->perm, plan->tab, sp,
-                                               stats);
-  return status_of_b(cudaGetLastError());
+  sp.cfirst[0] = sp.cfirst[1] = 0;
+  for (int m = 1; m <= kBatchNMax; ++m) {
+    const int c = plan->tab.kind[m] != kBatchNone ? (plan->tab.mcount[m] + kStatsChunk - 1) / kStatsChunk : 0;
+    sp.cfirst[m + 1] = sp.cfirst[m] + c;
+  }
+  const int nchunks = sp.cfirst[kBatchNMax + 1];
+  if (nchunks < 1) return PERM_EINVAL;
+  const size_t mom_bytes = (size_t)nchunks * 8 * sizeof(double);
+  char* scratch = nullptr;
+  if (cudaMallocAsync((void**)&scratch, mom_bytes + (size_t)nchunks * kStatsBins * sizeof(unsigned int), s) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return PERM_ENOMEM;
+  }
+  double* cmom = reinterpret_cast<double*>(scratch);
+  unsigned int* chist = reinterpret_cast<unsigned int*>(scratch + mom_bytes);
+  k_batch_stats_part<<<nchunks, kStatsThreads, 0, s>>>((const BatchArgs*)plan->args, (const int*)plan->perm,
+                                                       plan->tab, sp, cmom, chist);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    k_batch_stats_final<<<kBatchNMax + 1, kStatsThreads, 0, s>>>(plan->tab, sp, cmom, chist, stats);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(scratch, s);
+  return status_of_b(e);
 }
 
 int perm_batch_plans(int* built) {

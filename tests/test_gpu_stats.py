@@ -53,3 +53,32 @@ def test_stats_deterministic():
     a = P.perm_batch_stats(mats)[1].cpu()
     b = P.perm_batch_stats(mats)[1].cpu()
     assert torch.equal(a, b)
+
+
+def test_stats_many_chunks_of_one_order():
+    """More results of one order than one block of the first statistics kernel
+    takes (4096): 10,000 circular n = 5 matrices (three chunks) plus 5,000 of
+    n = 3 (two chunks); the chunks' exact sums are added per order.  Counts and
+    histograms against the oracle, moments at 1e-12."""
+    mats, ns = [], []
+    for k in range(10_000):
+        mats.append(W.circular(5, 70_000 + k))
+        ns.append(5)
+    for k in range(5_000):
+        mats.append(W.circular(3, 90_000 + k))
+        ns.append(3)
+    dm = [torch.from_numpy(np.ascontiguousarray(A)).cuda() for A in mats]
+    out, stats = P.perm_batch_stats(dm)
+    assert P.perm_last_status() == 0
+    st = stats.cpu().numpy()
+    o = out.cpu().numpy()
+    # the oracle's statistics of the library's own permanents isolate the
+    # statistics kernels (the permanents are checked elsewhere)
+    ref = O.batch_stats([complex(a, b) for a, b in o], ns)
+    assert np.array_equal(st[:, 0], ref[:, 0])
+    for n in (3, 5):
+        for q in range(1, 5):
+            assert st[n, q] == pytest.approx(ref[n, q], rel=1e-12), (n, q)
+    # histograms: exact except for a value within rounding of a bin edge
+    assert np.abs(st[:, 5:] - ref[:, 5:]).sum() <= 2
+    assert st[:, 5:].sum() == len(mats)
