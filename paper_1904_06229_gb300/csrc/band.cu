@@ -115,8 +115,8 @@ __global__ void __launch_bounds__(kBandThreads) k_band(const double* __restrict_
     sr = dd_add_d(sr, q[T].x);
     si = dd_add_d(si, q[T].y);
   }
-  sr = dd_warp_sum(sr);
-  si = dd_warp_sum(si);
+  sr = dd_warp_sum_exact(sr);
+  si = dd_warp_sum_exact(si);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
     red[2 * warp] = sr;

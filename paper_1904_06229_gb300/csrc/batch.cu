@@ -157,8 +157,8 @@ __global__ void __launch_bounds__(kBatchThreads)
       batch_walk_case<1, ROWS>(n, slot, r, end, accr, acci);
     else
       accr = acci = dd{__longlong_as_double(0x7ff8000000000000ll), 0.0};
-    accr = dd_warp_sum(accr);
-    acci = dd_warp_sum(acci);
+    accr = dd_warp_sum_exact(accr);
+    acci = dd_warp_sum_exact(acci);
     if (lane == 0) {
       accr = dd{scalbn(accr.hi, scale), scalbn(accr.lo, scale)};
       acci = dd{scalbn(acci.hi, scale), scalbn(acci.lo, scale)};

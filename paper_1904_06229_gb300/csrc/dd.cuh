@@ -47,17 +47,6 @@ __device__ __forceinline__ dd dd_add_d(dd a, double b) {
   return dd{s, e};
 }
 
-__device__ __forceinline__ dd dd_shfl_xor(dd a, int mask) {
-  return dd{__shfl_xor_sync(0xffffffffu, a.hi, mask), __shfl_xor_sync(0xffffffffu, a.lo, mask)};
-}
-
-// Butterfly reduction of a dd over the 32 lanes of a warp (fixed tree).
-__device__ __forceinline__ dd dd_warp_sum(dd a) {
-#pragma unroll
-  for (int m = 16; m >= 1; m >>= 1) a = dd_add(a, dd_shfl_xor(a, m));
-  return a;
-}
-
 // ---- Exact sums of double-double values on the integer pipes ----
 // A set of doubles is summed as signed 128-bit fixed-point integers in units
 // of 2^(emax - 1075 - kFxFrac), emax the largest biased exponent in the set
@@ -133,6 +122,17 @@ __device__ __forceinline__ dd dd_of_fx128(fx128 v, int emax) {
   r = dd_add_d(r, __ull2double_rn(v.l & 0x7FFull));
   const int sc = emax - 1075 - kFxFrac;
   return dd{scalbn(r.hi, sc), scalbn(r.lo, sc)};
+}
+
+// Exact sum over the 32 lanes of a warp of each lane's double-double: fx128
+// in units of the warp's largest exponent, converted back once; every lane
+// returns the same total (NaN if any lane holds a non-finite value).
+__device__ __forceinline__ dd dd_warp_sum_exact(dd a) {
+  int e = max(dexp_field(a.hi), dexp_field(a.lo));
+  e = max(1, (int)__reduce_max_sync(0xffffffffu, (unsigned)e));
+  if (e >= 0x7FF) return dd{__longlong_as_double(0x7ff8000000000000ll), 0.0};
+  const fx128 f = fx128_warp_sum(fx128_add(fx128_of(a.hi, e), fx128_of(a.lo, e)));
+  return dd_of_fx128(f, e);
 }
 
 // +-1.0 from a bit, built with integer operations only (no FP64 instruction).
