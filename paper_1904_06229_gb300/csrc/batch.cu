@@ -157,11 +157,9 @@ __global__ void __launch_bounds__(kBatchThreads)
       batch_walk_case<1, ROWS>(n, slot, r, end, accr, acci);
     else
       accr = acci = dd{__longlong_as_double(0x7ff8000000000000ll), 0.0};
-    accr = dd_warp_sum_exact(accr);
-    acci = dd_warp_sum_exact(acci);
+    accr = dd_warp_sum_exact(accr, scale);  // the rows' scales applied in the exponent
+    acci = dd_warp_sum_exact(acci, scale);
     if (lane == 0) {
-      accr = dd{scalbn(accr.hi, scale), scalbn(accr.lo, scale)};
-      acci = dd{scalbn(acci.hi, scale), scalbn(acci.lo, scale)};
       double* o = partials + item.partial * 4;
       o[0] = accr.hi;
       o[1] = accr.lo;

@@ -110,29 +110,106 @@ __device__ __forceinline__ fx128 fx128_warp_sum(fx128 a) {
   return a;
 }
 
-// The fixed-point value v (units 2^(emax - 1075 - kFxFrac)) as a double-double:
-// v = h 2^64 + l split into four exact doubles (h rounded to 53 bits and its
-// remainder, the top 53 and the low 11 bits of l), summed in order.
-__device__ __forceinline__ dd dd_of_fx128(fx128 v, int emax) {
+// Round to nearest (ties to even) of the unsigned 128-bit integer (mh, ml)
+// times 2^ex, with integer instructions only: the double's magnitude bits, and
+// the remainder m - RN(m) in units of 2^ex as a sign and a 128-bit magnitude.
+// False when the double would not be normal.
+__device__ __forceinline__ bool u128_rn(unsigned long long mh, unsigned long long ml, int ex,
+                                        unsigned long long& bits, unsigned& rneg, unsigned long long& rh,
+                                        unsigned long long& rl) {
+  rneg = 0;
+  rh = rl = 0;
+  if ((mh | ml) == 0) {
+    bits = 0;
+    return true;
+  }
+  const int L = mh ? 128 - __clzll((long long)mh) : 64 - __clzll((long long)ml);  // bit length
+  unsigned long long mant;
+  int s = L - 53;  // the 53-bit significand is m 2^-s
+  if (s <= 0) {
+    mant = ml << (-s);  // exact
+  } else {
+    unsigned long long remh, reml, hh, hl, th, tl;
+    if (s >= 64) {
+      mant = mh >> (s - 64);
+      remh = s > 64 ? mh & ((1ull << (s - 64)) - 1) : 0;
+      reml = ml;
+      th = 1ull << (s - 64);
+      tl = 0;
+    } else {
+      mant = (mh << (64 - s)) | (ml >> s);
+      remh = 0;
+      reml = ml & ((1ull << s) - 1);
+      th = 0;
+      tl = 1ull << s;
+    }
+    if (s - 1 >= 64) {
+      hh = 1ull << (s - 65);
+      hl = 0;
+    } else {
+      hh = 0;
+      hl = 1ull << (s - 1);
+    }
+    const bool gt = remh > hh || (remh == hh && reml > hl);
+    const bool eq = remh == hh && reml == hl;
+    if (gt || (eq && (mant & 1ull))) {  // round up: the remainder is rem - 2^s
+      ++mant;
+      rneg = 1;
+      rl = tl - reml;
+      rh = th - remh - (tl < reml ? 1ull : 0ull);
+    } else {
+      rh = remh;
+      rl = reml;
+    }
+    if (mant == (1ull << 53)) {
+      mant >>= 1;
+      ++s;
+    }
+  }
+  const int biased = 1075 + s + ex;
+  if (biased < 1 || biased > 2046) return false;
+  bits = ((unsigned long long)biased << 52) | (mant & ((1ull << 52) - 1));
+  return true;
+}
+
+// The fixed-point value v (units 2^(emax - 1075 - kFxFrac + extra)) as the
+// double-double (RN(v), RN(v - RN(v))), with integer instructions; values
+// outside the normal double range take an FP64 route instead (v = h 2^64 + l
+// split into four exact doubles, summed in order, scaled by scalbn).
+__device__ __forceinline__ dd dd_of_fx128(fx128 v, int emax, int extra = 0) {
+  const int ex = emax - 1075 - kFxFrac + extra;
+  unsigned long long h = (unsigned long long)v.h, l = v.l;
+  const unsigned neg = (unsigned)(h >> 63);
+  if (neg) {
+    l = ~l + 1ull;
+    h = ~h + (l == 0ull ? 1ull : 0ull);
+  }
+  unsigned long long hb, lb, rh, rl, t1, t2;
+  unsigned rneg, t0;
+  if (u128_rn(h, l, ex, hb, rneg, rh, rl) && u128_rn(rh, rl, ex, lb, t0, t1, t2)) {
+    const double hi = __longlong_as_double((long long)(hb | ((unsigned long long)neg << 63)));
+    const double lo = lb ? __longlong_as_double((long long)(lb | ((unsigned long long)(neg ^ rneg) << 63))) : 0.0;
+    return dd{hi, lo};
+  }
   const double ph = __ll2double_rn(v.h);  // |v.h| < 2^58: the conversion back is exact
-  const long long rh = v.h - __double2ll_rn(ph);
+  const long long rh2 = v.h - __double2ll_rn(ph);
   dd r{ph * 0x1p64, 0.0};
-  r = dd_add_d(r, (double)rh * 0x1p64);
+  r = dd_add_d(r, (double)rh2 * 0x1p64);
   r = dd_add_d(r, __ull2double_rn(v.l & ~0x7FFull));
   r = dd_add_d(r, __ull2double_rn(v.l & 0x7FFull));
-  const int sc = emax - 1075 - kFxFrac;
-  return dd{scalbn(r.hi, sc), scalbn(r.lo, sc)};
+  return dd{scalbn(r.hi, ex), scalbn(r.lo, ex)};
 }
 
 // Exact sum over the 32 lanes of a warp of each lane's double-double: fx128
-// in units of the warp's largest exponent, converted back once; every lane
-// returns the same total (NaN if any lane holds a non-finite value).
-__device__ __forceinline__ dd dd_warp_sum_exact(dd a) {
+// in units of the warp's largest exponent, converted back once (times
+// 2^extra); every lane returns the same total (NaN if any lane holds a
+// non-finite value).
+__device__ __forceinline__ dd dd_warp_sum_exact(dd a, int extra = 0) {
   int e = max(dexp_field(a.hi), dexp_field(a.lo));
   e = max(1, (int)__reduce_max_sync(0xffffffffu, (unsigned)e));
   if (e >= 0x7FF) return dd{__longlong_as_double(0x7ff8000000000000ll), 0.0};
   const fx128 f = fx128_warp_sum(fx128_add(fx128_of(a.hi, e), fx128_of(a.lo, e)));
-  return dd_of_fx128(f, e);
+  return dd_of_fx128(f, e, extra);
 }
 
 // +-1.0 from a bit, built with integer operations only (no FP64 instruction).
