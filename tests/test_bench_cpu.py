@@ -1,5 +1,6 @@
 """The bench's reference arm (the CPU oracle timed on the host cores) and its
-argument checks, on the CPU: one JSON line with the contract's keys."""
+argument checks, on the CPU: one JSON line with the contract's keys; the
+roofline's operation counts."""
 import json
 import os
 import subprocess
@@ -34,3 +35,22 @@ def test_warmup_below_three_is_refused():
     r = _run("--impl", "reference", "--steps", "1", "--warmup", "2", timeout=120)
     assert r.returncode != 0
     assert "warmup" in (r.stderr + r.stdout)
+
+
+def test_fp32_operation_counts_of_the_roofline():
+    """The roofline's FP32 operations per code, hand-counted from the default
+    walk's arithmetic: per row pair and step two 11-operation packed
+    double-float adds (22 packed = 44 lane operations), NP - 1 packed complex
+    products of 32 (64 lane operations), a 4-operation packed renormalisation
+    at the end of each of the three chain pairs and every 8 factors of a chain
+    that continues (8 lane operations each), and a 32-operation scalar join.
+    n = 40: NP = 20, chains of 7, 7, 6 factors, no mid-chain renormalisation:
+    880 + 1216 + 24 + 32.  n = 48: chains of 8, 8, 8 (the 8th is each chain's
+    last), 1056 + 1472 + 24 + 32.  n = 64: chains of 11, 11, 10, one
+    mid-chain renormalisation each, 1408 + 1984 + 48 + 32."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.pdf_fp32_ops(40) == 2152
+    assert bench.pdf_fp32_ops(48) == 2584
+    assert bench.pdf_fp32_ops(64) == 3472
